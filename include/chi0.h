@@ -1,0 +1,184 @@
+/*
+ * chi0.h -- C ABI of the GB300 (sm_103a) library that computes the RPA
+ * independent-particle polarizability chi0_{GG'}(q, w) and the inverse
+ * symmetric dielectric matrix eps~^-1(q, w) of the GW/BSE method described in
+ * Sangalli et al., "Many-body perturbation theory calculations using the yambo
+ * code", J. Phys.: Condens. Matter 31, 325902 (2019), arXiv:1902.03837.
+ *
+ * The operations (paper sections / equations):
+ *   - oscillator strengths  rho_{nmk}(q,G) = <n k| e^{i(q+G).r} |m k-q>,
+ *     Linear Response section, Eq. (rhotw), evaluated through the
+ *     real-space product of the two states and a Fourier transform;
+ *   - chi0_{GG'}(q,w) = f_s/(N_k Omega) sum_{nmk} rho rho^* x (two-pole
+ *     frequency factor), Eq. (X_IP), organised as in Appendix B, Eqs.
+ *     (X_IP_split), (X_IP_split1), (X_IP_split2): frequency-independent
+ *     rho rho^* products weighted by per-transition frequency factors;
+ *   - the Dyson step of the Linear Algebra subsection, Eqs. (X_rpa) and
+ *     (X_rpa_inv), written for the symmetric matrix
+ *     eps~ = 1 - v^1/2 chi0 v^1/2, v(q+G) = 4 pi / |q+G|^2 (Coulomb
+ *     interaction subsection), whose inverse gives W through Eq. (W_def).
+ *
+ * Units: Hartree atomic units (Ha, bohr).  Complex numbers are interleaved
+ * (re, im).  All arrays are row-major (C order).
+ *
+ * Conventions fixed by this library (readings of the paper):
+ *   - n is the band at k and m the band at k - q (as in Eq. rhotw); k - q is
+ *     folded to the grid as k - q = k' + G0 with the periodic gauge
+ *     psi_{k'+G0} = psi_{k'};
+ *   - time-reversal two-pole form: transitions t = (k, n, m) with weight
+ *     w_t(w) = f_s/(N_k Omega) (f_{m,k-q} - f_{n,k})
+ *              [1/(w + D_t + i eta) - 1/(w - D_t + i eta)],
+ *     D_t = eps_{m,k-q} - eps_{n,k}; chi0(w) = sum_t w_t rho_t rho_t^H.  Pairs
+ *     with f_{m,k-q} - f_{n,k} <= occ_drop_tol carry zero weight;
+ *   - the response G set is the ng vectors of smallest |q+G|, ties broken by
+ *     ascending (Gx, Gy, Gz), |q+G|^2 compared exactly;
+ *   - only Hermitian cases are supported (time-reversal-symmetric inputs and
+ *     real weights: imaginary frequencies with eta = 0, or w = 0 with any eta);
+ *     other frequencies return CHI0_EUNSUPPORTED.
+ *
+ * Asynchrony: every call that launches work is asynchronous on
+ * config.cuda_stream (NULL = the legacy default stream).  The returned status
+ * covers argument checks and launch errors; errors raised on the device are
+ * reported by the next call that synchronises (chi0_synchronize, or a call
+ * that copies results to the host).
+ *
+ * Errors never abort the process: every call returns a chi0_status and
+ * chi0_last_error() describes the most recent failure on that context.
+ */
+#ifndef CHI0_H_
+#define CHI0_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chi0_ctx chi0_ctx; /* opaque */
+
+typedef enum {
+  CHI0_OK = 0,
+  CHI0_EINVAL = -1,       /* bad argument (NULL pointer, size out of range, ...) */
+  CHI0_ENOMEM = -2,       /* device or host allocation failed */
+  CHI0_ECUDA = -3,        /* a CUDA runtime/driver call failed */
+  CHI0_ESTATE = -4,       /* call out of order (see "Ordering" below) */
+  CHI0_ENOTPD = -5,       /* a pivot of the Dyson elimination vanished or eps~ not positive */
+  CHI0_ESINGULAR = -6,    /* reserved: singular matrix in a general solve */
+  CHI0_ETIMEOUT = -7,     /* a bounded device-side wait gave up (error flag set by a kernel) */
+  CHI0_EUNSUPPORTED = -8  /* valid request outside what this build implements */
+} chi0_status;
+
+typedef enum {
+  CHI0_FP64 = 0,          /* FP64 end to end (rho, contraction, Dyson) */
+  CHI0_MIXED_BF16X3 = 1   /* FP32 rho, split-precision BF16x3 tensor-core contraction
+                             accumulated in FP32 over bounded transition chunks and
+                             summed in FP64, FP64 Dyson */
+} chi0_precision;
+
+typedef struct {
+  double lattice[3][3];   /* bohr, rows a1, a2, a3; this build needs a cubic cell a*I */
+  int kgrid[3];           /* Gamma-centred grid, k = (i/N1, j/N2, l/N3), k index = (i*N2+j)*N3+l */
+  int nbands;             /* bands per k */
+  int npw_max;            /* largest plane-wave sphere over all k */
+  int fft[3];             /* real-space grid (N1, N2, N3) used for rho; must be alias free */
+  int ng;                 /* number of response G vectors */
+  int nq;                 /* number of q points */
+  const double* q_frac;   /* [nq][3] reduced coordinates; each q must be a vector of the k grid;
+                             copied at chi0_create */
+  int nw;                 /* number of frequencies */
+  const double* omega;    /* [nw][2] complex frequencies (re, im) in Ha; copied at chi0_create */
+  double eta;             /* Ha; +i*eta on both poles (retarded); 0 on the imaginary axis */
+  double spin_factor;     /* f_s: 2 without spin polarisation, 1 with it */
+  int precision;          /* chi0_precision */
+  int time_reversal;      /* must be 1: inputs obey psi_{-k} = psi_k^*, eps_{-k} = eps_k */
+  double occ_drop_tol;    /* transitions with f_m - f_n <= tol get zero weight (>= 0) */
+  void* cuda_stream;      /* cudaStream_t for all work; NULL = default stream */
+} chi0_config;
+
+/* Create a context.  Validates the configuration and copies q_frac and omega.
+ * Allocates nothing on the device yet.  *out receives the handle (NULL on
+ * failure).  Errors: CHI0_EINVAL, CHI0_EUNSUPPORTED (non-cubic cell,
+ * time_reversal != 1), CHI0_ENOMEM. */
+chi0_status chi0_create(const chi0_config* cfg, chi0_ctx** out);
+
+/* Plane-wave sphere and coefficients of every band at k point ik
+ * (the states of the paper's wavefunction databases, k-centred spheres).
+ *   gvec: [npw][3] int32 Miller indices of G with |k+G| < k_c (any order);
+ *   coef: [nbands][npw] complex coefficients c_{n,k}(G), interleaved, complex64
+ *         when coef_is_c64 = 1, else complex128;
+ *   on_device: 1 if gvec and coef are device pointers (copied device to device),
+ *              0 if host pointers (copied; pinned host memory makes the copy async).
+ * The data are copied (converted to the working precision when needed); the
+ * caller keeps ownership of its buffers, which may be reused once the call has
+ * returned for host pointers, or once the stream has passed this point for
+ * device pointers.  Errors: CHI0_EINVAL (ik or npw out of range, NULL),
+ * CHI0_ENOMEM, CHI0_ECUDA. */
+chi0_status chi0_set_wavefunctions(chi0_ctx* ctx, int ik, int npw, const int32_t* gvec,
+                                   const void* coef, int coef_is_c64, int on_device);
+
+/* Band energies eps[nk][nbands] (Ha) and occupations occ[nk][nbands] in [0,1]
+ * per spin channel (host pointers, copied).  Errors: CHI0_EINVAL. */
+chi0_status chi0_set_energies(chi0_ctx* ctx, const double* eps, const double* occ);
+
+/* Oscillator strengths rho_t(G_i), Eq. (rhotw), for every transition of the
+ * time-reversal form at q index iq; kept on the device as R[nt][ng] (G fastest;
+ * complex128 in FP64 mode, complex64 in mixed mode).  Requires all
+ * wavefunctions and energies.  Errors: CHI0_ESTATE, CHI0_EINVAL, CHI0_ENOMEM,
+ * CHI0_ECUDA. */
+chi0_status chi0_compute_rho(chi0_ctx* ctx, int iq);
+
+/* chi0(q_iq, w) for every configured frequency, Eq. (X_IP) in the App. B
+ * organisation.  out: [nw][ng][ng] complex128, row index G, column index G'.
+ * out_on_device = 1: out is a device pointer (written asynchronously);
+ * 0: host pointer (this call synchronises); out may be NULL to keep chi0 on
+ * the device only (the Dyson step reads it from there).  Requires
+ * chi0_compute_rho(iq).  Errors: CHI0_ESTATE, CHI0_EUNSUPPORTED (non-real
+ * weights), CHI0_ENOMEM, CHI0_ECUDA, CHI0_ETIMEOUT (host copies only). */
+chi0_status chi0_build_chi0(chi0_ctx* ctx, int iq, void* out, int out_on_device);
+
+/* eps~^-1(q_iq, w) = (1 - v^1/2 chi0 v^1/2)^-1 for every frequency, Eqs.
+ * (X_rpa), (X_rpa_inv) in the symmetric form of Eq. (W_def), by FP64
+ * Gauss-Jordan elimination (eps~ is Hermitian positive definite here).
+ * out: [nw][ng][ng] complex128 as for chi0_build_chi0 (NULL not allowed).
+ * Requires chi0_build_chi0(iq).  A vanishing pivot is reported as CHI0_ENOTPD
+ * by the next synchronising call.  Errors: CHI0_ESTATE, CHI0_EINVAL,
+ * CHI0_ENOTPD, CHI0_ENOMEM, CHI0_ECUDA. */
+chi0_status chi0_invert_eps(chi0_ctx* ctx, int iq, void* out, int out_on_device);
+
+/* The response G vectors used at q index iq, out: [ng][3] int32 (host).
+ * Errors: CHI0_EINVAL. */
+chi0_status chi0_get_response_gvectors(chi0_ctx* ctx, int iq, int32_t* out);
+
+/* The transition list of the last chi0_compute_rho: *nt receives the count;
+ * if out is not NULL it receives [nt][3] int32 triples (ik, n, m), in the row
+ * order of R.  Errors: CHI0_ESTATE. */
+chi0_status chi0_get_transitions(chi0_ctx* ctx, int64_t* nt, int32_t* out);
+
+/* Copy R = rho (the last chi0_compute_rho) to a host buffer out [nt][ng]
+ * complex128 (converted from complex64 in mixed mode).  Synchronises.
+ * Errors: CHI0_ESTATE, CHI0_ECUDA. */
+chi0_status chi0_get_rho(chi0_ctx* ctx, void* out);
+
+/* Wait for all work queued by this context and report device-side errors
+ * (CHI0_ETIMEOUT, CHI0_ENOTPD, CHI0_ECUDA). */
+chi0_status chi0_synchronize(chi0_ctx* ctx);
+
+/* Per-stage device times of the last calls (ms, CUDA events on the context's
+ * stream; stage 0 = rho, 1 = weights + contraction, 2 = reduce/finish,
+ * 3 = Dyson), their algorithmic bytes and flops.  Any pointer may be NULL.
+ * Synchronises. */
+chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms_per_stage /*[4]*/, double* bytes /*[4]*/,
+                           double* flops /*[4]*/);
+
+/* Text of the last error on ctx (static storage inside ctx; never NULL). */
+const char* chi0_last_error(const chi0_ctx* ctx);
+
+/* Release all device and host memory of ctx (synchronises its stream). */
+void chi0_destroy(chi0_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHI0_H_ */

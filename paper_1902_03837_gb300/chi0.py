@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libchi0 (include/chi0.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Host arrays are numpy arrays; device arrays are torch CUDA tensors
+(passed by data_ptr, kept alive by the caller).  Importing this module loads
+the library and raises if it has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchi0.so")
+
+CHI0_FP64 = 0
+CHI0_MIXED_BF16X3 = 1
+
+STATUS = {
+    0: "CHI0_OK", -1: "CHI0_EINVAL", -2: "CHI0_ENOMEM", -3: "CHI0_ECUDA", -4: "CHI0_ESTATE",
+    -5: "CHI0_ENOTPD", -6: "CHI0_ESINGULAR", -7: "CHI0_ETIMEOUT", -8: "CHI0_EUNSUPPORTED",
+}
+
+EXPORTS = (
+    "chi0_create", "chi0_set_wavefunctions", "chi0_set_energies", "chi0_compute_rho",
+    "chi0_build_chi0", "chi0_invert_eps", "chi0_get_response_gvectors", "chi0_get_transitions",
+    "chi0_get_rho", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
+)
+
+
+class Chi0Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Chi0Config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_double * 9),
+        ("kgrid", ctypes.c_int * 3),
+        ("nbands", ctypes.c_int),
+        ("npw_max", ctypes.c_int),
+        ("fft", ctypes.c_int * 3),
+        ("ng", ctypes.c_int),
+        ("nq", ctypes.c_int),
+        ("q_frac", ctypes.POINTER(ctypes.c_double)),
+        ("nw", ctypes.c_int),
+        ("omega", ctypes.POINTER(ctypes.c_double)),
+        ("eta", ctypes.c_double),
+        ("spin_factor", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("time_reversal", ctypes.c_int),
+        ("occ_drop_tol", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libchi0.so not built at {path}: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.chi0_create.argtypes = [ctypes.POINTER(Chi0Config), ctypes.POINTER(P)]
+    lib.chi0_set_wavefunctions.argtypes = [P, I, I, P, P, I, I]
+    lib.chi0_set_energies.argtypes = [P, P, P]
+    lib.chi0_compute_rho.argtypes = [P, I]
+    lib.chi0_build_chi0.argtypes = [P, I, P, I]
+    lib.chi0_invert_eps.argtypes = [P, I, P, I]
+    lib.chi0_get_response_gvectors.argtypes = [P, I, P]
+    lib.chi0_get_transitions.argtypes = [P, ctypes.POINTER(I64), P]
+    lib.chi0_get_rho.argtypes = [P, P]
+    lib.chi0_synchronize.argtypes = [P]
+    lib.chi0_get_stats.argtypes = [P, P, P, P]
+    lib.chi0_last_error.argtypes = [P]
+    lib.chi0_last_error.restype = ctypes.c_char_p
+    lib.chi0_destroy.argtypes = [P]
+    lib.chi0_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("chi0_last_error", "chi0_destroy"):
+            getattr(lib, name).restype = I
+    del D
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor (must be contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class Chi0:
+    """One chi0_ctx.  Method names follow the C entry points."""
+
+    def __init__(self, *, a, kgrid, nbands, npw_max, fft, ng, q_frac, omega, eta,
+                 spin_factor=2.0, precision=CHI0_FP64, time_reversal=1, occ_drop_tol=0.0,
+                 stream=None):
+        cfg = Chi0Config()
+        lat = np.eye(3) * float(a)
+        cfg.lattice[:] = lat.ravel().tolist()
+        cfg.kgrid[:] = [int(v) for v in kgrid]
+        cfg.nbands = int(nbands)
+        cfg.npw_max = int(npw_max)
+        cfg.fft[:] = [int(v) for v in fft]
+        cfg.ng = int(ng)
+        self._q = np.ascontiguousarray(np.asarray(q_frac, dtype=np.float64).reshape(-1, 3))
+        om = np.asarray(omega, dtype=np.complex128).reshape(-1)
+        self._om = np.ascontiguousarray(np.stack([om.real, om.imag], axis=1))
+        cfg.nq = self._q.shape[0]
+        cfg.q_frac = self._q.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.nw = self._om.shape[0]
+        cfg.omega = self._om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.eta = float(eta)
+        cfg.spin_factor = float(spin_factor)
+        cfg.precision = int(precision)
+        cfg.time_reversal = int(time_reversal)
+        cfg.occ_drop_tol = float(occ_drop_tol)
+        cfg.cuda_stream = stream
+        self.cfg = cfg
+        self.nk = int(np.prod(kgrid))
+        self.nb = int(nbands)
+        self.ng = int(ng)
+        self.nw = cfg.nw
+        self.precision = int(precision)
+        h = ctypes.c_void_p()
+        st = _lib.chi0_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise Chi0Error(st, "chi0_create rejected the configuration")
+        self.h = h
+
+    # -- helpers
+    def _check(self, st):
+        if st != 0:
+            raise Chi0Error(st, _lib.chi0_last_error(self.h).decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.chi0_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points
+    def set_wavefunctions(self, ik, gvec, coef):
+        """gvec [npw][3] int32, coef [nbands][npw] complex64/complex128 (numpy or torch)."""
+        gp, gdev = _ptr(gvec)
+        cp, cdev = _ptr(coef)
+        if gdev != cdev:
+            raise ValueError("gvec and coef must both be host or both be device buffers")
+        if isinstance(coef, np.ndarray):
+            c64 = coef.dtype == np.complex64
+            npw = coef.shape[1]
+        else:
+            import torch
+            c64 = coef.dtype == torch.complex64
+            npw = coef.shape[1]
+        self._check(_lib.chi0_set_wavefunctions(self.h, int(ik), int(npw), gp, cp, int(c64), cdev))
+
+    def set_energies(self, eps, occ):
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        self._check(_lib.chi0_set_energies(self.h, eps.ctypes.data, occ.ctypes.data))
+
+    def compute_rho(self, iq):
+        self._check(_lib.chi0_compute_rho(self.h, int(iq)))
+
+    def build_chi0(self, iq, out=None):
+        """out: None (keep on device), numpy complex128 [nw][ng][ng] or a torch tensor."""
+        if out is None:
+            self._check(_lib.chi0_build_chi0(self.h, int(iq), None, 1))
+            return None
+        p, dev = _ptr(out)
+        self._check(_lib.chi0_build_chi0(self.h, int(iq), p, dev))
+        return out
+
+    def invert_eps(self, iq, out):
+        p, dev = _ptr(out)
+        self._check(_lib.chi0_invert_eps(self.h, int(iq), p, dev))
+        return out
+
+    def get_response_gvectors(self, iq):
+        out = np.zeros((self.ng, 3), dtype=np.int32)
+        self._check(_lib.chi0_get_response_gvectors(self.h, int(iq), out.ctypes.data))
+        return out
+
+    def get_transitions(self):
+        nt = ctypes.c_int64()
+        self._check(_lib.chi0_get_transitions(self.h, ctypes.byref(nt), None))
+        out = np.zeros((nt.value, 3), dtype=np.int32)
+        self._check(_lib.chi0_get_transitions(self.h, ctypes.byref(nt), out.ctypes.data))
+        return out
+
+    def get_rho(self):
+        nt = ctypes.c_int64()
+        self._check(_lib.chi0_get_transitions(self.h, ctypes.byref(nt), None))
+        out = np.zeros((nt.value, self.ng), dtype=np.complex128)
+        self._check(_lib.chi0_get_rho(self.h, out.ctypes.data))
+        return out
+
+    def synchronize(self):
+        self._check(_lib.chi0_synchronize(self.h))
+
+    def get_stats(self):
+        ms = np.zeros(4)
+        by = np.zeros(4)
+        fl = np.zeros(4)
+        self._check(_lib.chi0_get_stats(self.h, ms.ctypes.data, by.ctypes.data, fl.ctypes.data))
+        return ms, by, fl
+
+    # -- convenience: marshal a synthetic system's arrays
+    @classmethod
+    def for_system(cls, system, precision=CHI0_FP64, stream=None, occ_drop_tol=0.0, **over):
+        kw = dict(a=system.spec.a, kgrid=system.spec.kgrid, nbands=system.nb,
+                  npw_max=system.npw_max, fft=system.fft, ng=system.ng, q_frac=system.q_frac,
+                  omega=system.freqs, eta=system.eta, spin_factor=system.spin_factor,
+                  precision=precision, occ_drop_tol=occ_drop_tol, stream=stream)
+        kw.update(over)
+        return cls(**kw)
+
+    def load_system(self, system):
+        for ik in range(system.nk):
+            n = int(system.npw[ik])
+            self.set_wavefunctions(ik, np.ascontiguousarray(system.gvec[ik, :n]),
+                                   np.ascontiguousarray(system.coef[ik, :, :n]))
+        self.set_energies(system.eps, system.occ)

@@ -1,0 +1,682 @@
+// C ABI of libchi0 (declared in include/chi0.h): argument checking, the host
+// side of the q-point setup (k - q folding, response G set, transition block,
+// twiddle tables) and the stream-ordered sequence of kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/chi0.h"
+#include "ctx.cuh"
+
+using chi0::RhoGeom;
+
+namespace {
+
+chi0_status fail(chi0_ctx* c, chi0_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+chi0_status cuda_fail(chi0_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? CHI0_ENOMEM : CHI0_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+chi0_status ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return CHI0_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (std::getenv("CHI0_FAULT") && std::strcmp(std::getenv("CHI0_FAULT"), "alloc") == 0)
+    return fail(c, CHI0_ENOMEM, "%s: injected allocation failure (CHI0_FAULT=alloc)", what);
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CHI0_ENOMEM, "%s: cudaMalloc(%zu) failed: %s", what, bytes,
+                cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return CHI0_OK;
+}
+
+}  // namespace
+
+namespace chi0 {
+chi0_status ctx_fail(chi0_ctx* c, chi0_status s, const char* msg) { c->err = msg; return s; }
+chi0_status ctx_ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) { return ensure(c, b, bytes, what); }
+}  // namespace chi0
+
+namespace {
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+size_t cplx_bytes(const chi0_ctx* c) { return c->fp64 ? 16 : 8; }
+
+// |q+G|^2 scaled to an exact integer for a cubic cell: sum_a (L q_a + L G_a)^2
+// with L = lcm of the k grid (q is a grid vector, so L q_a is an integer).
+int64_t lcm64(int64_t a, int64_t b) {
+  int64_t x = a, y = b;
+  while (y) {
+    int64_t t = x % y;
+    x = y;
+    y = t;
+  }
+  return a / x * b;
+}
+
+bool q_integers(const chi0_ctx* c, int iq, int64_t qi[3]) {
+  for (int d = 0; d < 3; ++d) {
+    const double x = c->q[3 * iq + d] * c->cfg.kgrid[d];
+    const double r = std::nearbyint(x);
+    if (std::fabs(x - r) > 1e-9) return false;
+    qi[d] = (int64_t)r;
+  }
+  return true;
+}
+
+void response_set(const chi0_ctx* c, int iq, std::vector<int32_t>& out) {
+  int64_t qi[3];
+  q_integers(c, iq, qi);
+  const int64_t L = lcm64(lcm64(c->cfg.kgrid[0], c->cfg.kgrid[1]), c->cfg.kgrid[2]);
+  int64_t lq[3];
+  for (int d = 0; d < 3; ++d) lq[d] = qi[d] * (L / c->cfg.kgrid[d]);
+  const int ng = c->cfg.ng;
+  const int m = (int)std::ceil(std::cbrt(3.0 * ng / (4.0 * M_PI))) + 3;
+  std::vector<std::tuple<int64_t, int, int, int>> cand;
+  cand.reserve((size_t)(2 * m + 1) * (2 * m + 1) * (2 * m + 1));
+  for (int x = -m; x <= m; ++x)
+    for (int y = -m; y <= m; ++y)
+      for (int z = -m; z <= m; ++z) {
+        const int64_t a = lq[0] + L * x, b = lq[1] + L * y, d = lq[2] + L * z;
+        cand.emplace_back(a * a + b * b + d * d, x, y, z);
+      }
+  std::sort(cand.begin(), cand.end());
+  out.resize((size_t)ng * 3);
+  for (int i = 0; i < ng; ++i) {
+    out[3 * i] = std::get<1>(cand[i]);
+    out[3 * i + 1] = std::get<2>(cand[i]);
+    out[3 * i + 2] = std::get<3>(cand[i]);
+  }
+}
+
+void kpairs(const chi0_ctx* c, int iq, std::vector<int32_t>& kq, std::vector<int32_t>& g0) {
+  int64_t qi[3];
+  q_integers(c, iq, qi);
+  const int* n = c->cfg.kgrid;
+  kq.resize(c->nk);
+  g0.resize((size_t)c->nk * 3);
+  for (int i = 0; i < n[0]; ++i)
+    for (int j = 0; j < n[1]; ++j)
+      for (int l = 0; l < n[2]; ++l) {
+        const int ik = (i * n[1] + j) * n[2] + l;
+        const int64_t src[3] = {i - qi[0], j - qi[1], l - qi[2]};
+        int64_t rep[3];
+        for (int d = 0; d < 3; ++d) {
+          rep[d] = ((src[d] % n[d]) + n[d]) % n[d];
+          g0[3 * ik + d] = (int32_t)((src[d] - rep[d]) / n[d]);
+        }
+        kq[ik] = (int32_t)((rep[0] * n[1] + rep[1]) * n[2] + rep[2]);
+      }
+}
+
+template <typename T2>
+void twiddles(int n, std::vector<T2>& out) {
+  out.resize(n);
+  for (int j = 0; j < n; ++j) {
+    const double ang = 2.0 * M_PI * (double)j / (double)n;
+    out[j].x = std::cos(ang);
+    out[j].y = std::sin(ang);
+  }
+}
+
+void record(chi0_ctx* c, int stage, bool start) {
+  cudaEvent_t& ev = c->ev[2 * stage + (start ? 0 : 1)];
+  if (!ev && cudaEventCreate(&ev) != cudaSuccess) {
+    cudaGetLastError();
+    ev = nullptr;
+    return;
+  }
+  cudaEventRecord(ev, c->st);
+  if (!start) c->ev_pending[stage] = true;
+}
+
+chi0_status check_device_error(chi0_ctx* c) {
+  if (!c->d_err.p) return CHI0_OK;
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, c->d_err.p, sizeof(h), cudaMemcpyDeviceToHost, c->st), "read error flag");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  if (h[0] || h[1]) {
+    CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(h), c->st), "clear error flag");
+    if (h[1]) return fail(c, CHI0_ETIMEOUT, "a bounded device-side wait gave up (code %d)", h[1]);
+    return fail(c, CHI0_ENOTPD, "Dyson elimination met a non-positive pivot: eps~ not HPD");
+  }
+  return CHI0_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+chi0_status chi0_create(const chi0_config* cfg, chi0_ctx** out) {
+  if (!out) return CHI0_EINVAL;
+  *out = nullptr;
+  if (!cfg) return CHI0_EINVAL;
+  chi0_ctx* c = new (std::nothrow) chi0_ctx();
+  if (!c) return CHI0_ENOMEM;
+  chi0_status s = CHI0_OK;
+  auto bad = [&](chi0_status st, const char* m) {
+    s = st;
+    c->err = m;
+  };
+  const double a = cfg->lattice[0][0];
+  for (int i = 0; i < 3 && s == CHI0_OK; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (std::fabs(cfg->lattice[i][j] - (i == j ? a : 0.0)) > 1e-12 * std::fabs(a))
+        bad(CHI0_EUNSUPPORTED, "only cubic cells a*I are supported");
+  if (s == CHI0_OK && !(a > 0)) bad(CHI0_EINVAL, "lattice constant must be positive");
+  for (int d = 0; d < 3 && s == CHI0_OK; ++d) {
+    if (cfg->kgrid[d] < 1 || cfg->kgrid[d] > 1024) bad(CHI0_EINVAL, "kgrid out of range");
+    if (cfg->fft[d] < 2 || cfg->fft[d] > 4096) bad(CHI0_EINVAL, "fft grid out of range");
+  }
+  if (s == CHI0_OK && (cfg->nbands < 1 || cfg->npw_max < 1 || cfg->ng < 1 || cfg->ng > 4096 ||
+                       cfg->nq < 1 || cfg->nw < 1 || !cfg->q_frac || !cfg->omega))
+    bad(CHI0_EINVAL, "nbands/npw_max/ng/nq/nw out of range or NULL q_frac/omega");
+  if (s == CHI0_OK && cfg->time_reversal != 1)
+    bad(CHI0_EUNSUPPORTED, "only time-reversal-symmetric inputs are supported");
+  if (s == CHI0_OK && cfg->precision != CHI0_FP64 && cfg->precision != CHI0_MIXED_BF16X3)
+    bad(CHI0_EINVAL, "unknown precision");
+  if (s == CHI0_OK && (cfg->occ_drop_tol < 0 || cfg->eta < 0 || !(cfg->spin_factor > 0)))
+    bad(CHI0_EINVAL, "occ_drop_tol, eta must be >= 0 and spin_factor > 0");
+  if (s != CHI0_OK) {
+    // the handle is not returned; the message cannot be read back
+    delete c;
+    return s;
+  }
+  c->cfg = *cfg;
+  c->q.assign(cfg->q_frac, cfg->q_frac + 3 * cfg->nq);
+  c->om.assign(cfg->omega, cfg->omega + 2 * cfg->nw);
+  c->cfg.q_frac = nullptr;
+  c->cfg.omega = nullptr;
+  c->nk = cfg->kgrid[0] * cfg->kgrid[1] * cfg->kgrid[2];
+  c->nb = cfg->nbands;
+  c->npw_max = cfg->npw_max;
+  c->a = a;
+  c->omega_cell = a * a * a;
+  c->st = (cudaStream_t)cfg->cuda_stream;
+  c->fp64 = cfg->precision == CHI0_FP64;
+  for (int iq = 0; iq < cfg->nq; ++iq) {
+    int64_t qi[3];
+    if (!q_integers(c, iq, qi)) {
+      delete c;
+      return CHI0_EINVAL;
+    }
+  }
+  c->h_npw.assign(c->nk, 0);
+  c->h_gvec.assign((size_t)c->nk * c->npw_max * 3, 0);
+  c->wf_set.assign(c->nk, 0);
+  *out = c;
+  return CHI0_OK;
+}
+
+chi0_status chi0_set_wavefunctions(chi0_ctx* c, int ik, int npw, const int32_t* gvec,
+                                   const void* coef, int coef_is_c64, int on_device) {
+  if (!c) return CHI0_EINVAL;
+  if (ik < 0 || ik >= c->nk) return fail(c, CHI0_EINVAL, "ik %d out of range", ik);
+  if (npw < 1 || npw > c->npw_max) return fail(c, CHI0_EINVAL, "npw %d out of range", npw);
+  if (!gvec || !coef) return fail(c, CHI0_EINVAL, "NULL gvec or coef");
+  chi0_status s;
+  const size_t cb = cplx_bytes(c);
+  if ((s = ensure(c, c->d_coef, (size_t)c->nk * c->nb * c->npw_max * cb, "coefficients")) != CHI0_OK)
+    return s;
+  if ((s = ensure(c, c->d_gvec, (size_t)c->nk * c->npw_max * 3 * 4, "gvec")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_npw, (size_t)c->nk * 4, "npw")) != CHI0_OK) return s;
+  // Miller indices: keep a host copy (sphere extents, alias checks)
+  int32_t* hg = c->h_gvec.data() + (size_t)ik * c->npw_max * 3;
+  if (on_device) {
+    CK(cudaMemcpyAsync(hg, gvec, (size_t)npw * 12, cudaMemcpyDeviceToHost, c->st), "gvec D2H");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  } else {
+    std::memcpy(hg, gvec, (size_t)npw * 12);
+  }
+  std::memset(hg + (size_t)npw * 3, 0, (size_t)(c->npw_max - npw) * 12);
+  for (int p = 0; p < npw * 3; ++p)
+    if (hg[p] < -1000 || hg[p] > 1000) return fail(c, CHI0_EINVAL, "Miller index out of range");
+  c->h_npw[ik] = npw;
+  CK(cudaMemcpyAsync((char*)c->d_gvec.p + (size_t)ik * c->npw_max * 12, hg,
+                     (size_t)c->npw_max * 12, cudaMemcpyHostToDevice, c->st),
+     "gvec H2D");
+  CK(cudaMemcpyAsync((char*)c->d_npw.p + (size_t)ik * 4, &c->h_npw[ik], 4, cudaMemcpyHostToDevice,
+                     c->st),
+     "npw H2D");
+  // coefficients: rows of npw, padded to npw_max
+  const bool same = (coef_is_c64 != 0) == !c->fp64;
+  char* dst = (char*)c->d_coef.p + (size_t)ik * c->nb * c->npw_max * cb;
+  CK(cudaMemsetAsync(dst, 0, (size_t)c->nb * c->npw_max * cb, c->st), "zero coefficients");
+  if (same) {
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->npw_max * cb, coef, (size_t)npw * cb, (size_t)npw * cb,
+                         c->nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         c->st),
+       "coefficients copy");
+  } else {
+    // convert on the host (device sources are staged through the host)
+    const size_t in_cb = coef_is_c64 ? 8 : 16;
+    std::vector<char> src((size_t)c->nb * npw * in_cb);
+    if (on_device) {
+      CK(cudaMemcpyAsync(src.data(), coef, src.size(), cudaMemcpyDeviceToHost, c->st), "coef D2H");
+      CK(cudaStreamSynchronize(c->st), "synchronize");
+    } else {
+      std::memcpy(src.data(), coef, src.size());
+    }
+    std::vector<char> conv((size_t)c->nb * npw * cb);
+    const size_t n = (size_t)c->nb * npw * 2;
+    if (coef_is_c64) {
+      const float* f = (const float*)src.data();
+      double* d = (double*)conv.data();
+      for (size_t i = 0; i < n; ++i) d[i] = f[i];
+    } else {
+      const double* d = (const double*)src.data();
+      float* f = (float*)conv.data();
+      for (size_t i = 0; i < n; ++i) f[i] = (float)d[i];
+    }
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->npw_max * cb, conv.data(), (size_t)npw * cb,
+                         (size_t)npw * cb, c->nb, cudaMemcpyHostToDevice, c->st),
+       "coefficients copy");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  }
+  c->wf_set[ik] = 1;
+  c->rho_iq = c->chi_iq = c->eps_iq = -1;
+  return CHI0_OK;
+}
+
+chi0_status chi0_set_energies(chi0_ctx* c, const double* eps, const double* occ) {
+  if (!c) return CHI0_EINVAL;
+  if (!eps || !occ) return fail(c, CHI0_EINVAL, "NULL eps or occ");
+  const size_t n = (size_t)c->nk * c->nb;
+  for (size_t i = 0; i < n; ++i) {
+    if (!std::isfinite(eps[i])) return fail(c, CHI0_EINVAL, "non-finite energy at %zu", i);
+    if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return fail(c, CHI0_EINVAL, "occupation outside [0,1] at %zu", i);
+  }
+  c->h_eps.assign(eps, eps + n);
+  c->h_occ.assign(occ, occ + n);
+  chi0_status s;
+  if ((s = ensure(c, c->d_eps, n * 8, "eps")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_occ, n * 8, "occ")) != CHI0_OK) return s;
+  CK(cudaMemcpyAsync(c->d_eps.p, c->h_eps.data(), n * 8, cudaMemcpyHostToDevice, c->st), "eps H2D");
+  CK(cudaMemcpyAsync(c->d_occ.p, c->h_occ.data(), n * 8, cudaMemcpyHostToDevice, c->st), "occ H2D");
+  c->energies_set = true;
+  c->rho_iq = c->chi_iq = c->eps_iq = -1;
+  return CHI0_OK;
+}
+
+chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
+  if (!c) return CHI0_EINVAL;
+  if (iq < 0 || iq >= c->cfg.nq) return fail(c, CHI0_EINVAL, "iq %d out of range", iq);
+  for (int ik = 0; ik < c->nk; ++ik)
+    if (!c->wf_set[ik]) return fail(c, CHI0_ESTATE, "wavefunctions of k %d not set", ik);
+  if (!c->energies_set) return fail(c, CHI0_ESTATE, "energies not set");
+  chi0_status s;
+  // ---- q-point setup on the host
+  response_set(c, iq, c->h_gresp);
+  kpairs(c, iq, c->h_kq, c->h_g0);
+  const double tol = c->cfg.occ_drop_tol;
+  int mmax = -1, nmin = c->nb;
+  for (int ik = 0; ik < c->nk; ++ik)
+    for (int b = 0; b < c->nb; ++b) {
+      const double f = c->h_occ[(size_t)ik * c->nb + b];
+      if (f > tol) mmax = std::max(mmax, b);
+      if (f < 1.0 - tol) nmin = std::min(nmin, b);
+    }
+  c->Nm = mmax + 1;
+  c->n_lo = nmin;
+  c->Nn = c->nb - nmin;
+  c->nt = (int64_t)c->nk * c->Nn * c->Nm;
+  RhoGeom& g = c->geom;
+  g = RhoGeom{};
+  g.N1 = c->cfg.fft[0];
+  g.N2 = c->cfg.fft[1];
+  g.N3 = c->cfg.fft[2];
+  int L[3] = {0, 0, 0};
+  for (int ik = 0; ik < c->nk; ++ik)
+    for (int p = 0; p < c->h_npw[ik]; ++p)
+      for (int d = 0; d < 3; ++d)
+        L[d] = std::max(L[d], std::abs(c->h_gvec[((size_t)ik * c->npw_max + p) * 3 + d]));
+  g.Lx = L[0];
+  g.Ly = L[1];
+  g.Lz = L[2];
+  g.NX = 2 * L[0] + 1;
+  g.NY = 2 * L[1] + 1;
+  g.NZ = 2 * L[2] + 1;
+  g.nk = c->nk;
+  g.nb = c->nb;
+  g.npw_max = c->npw_max;
+  g.ng = c->cfg.ng;
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int i = 0; i < g.ng; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], c->h_gresp[3 * i + d]);
+      hi[d] = std::max(hi[d], c->h_gresp[3 * i + d]);
+    }
+  g.Mx_lo = lo[0];
+  g.My_lo = lo[1];
+  g.Mz_lo = lo[2];
+  g.HX = hi[0] - lo[0] + 1;
+  g.HY = hi[1] - lo[1] + 1;
+  g.HZ = hi[2] - lo[2] + 1;
+  g.n_lo = c->n_lo;
+  g.Nn = c->Nn;
+  g.Nm = c->Nm;
+  int g0max = 0;
+  for (int v : c->h_g0) g0max = std::max(g0max, std::abs(v));
+  g.g0max = g0max;
+  // the real-space product must not alias onto the response set
+  for (int d = 0; d < 3; ++d) {
+    const int n = c->cfg.fft[d];
+    const int hmax = std::max(std::abs(lo[d]), std::abs(hi[d])) + g0max;
+    if (n <= 2 * L[d] + hmax)
+      return fail(c, CHI0_EINVAL,
+                  "fft[%d] = %d aliases: need > 2*%d + %d for these spheres and response set", d,
+                  n, L[d], hmax);
+  }
+  if (c->nt == 0) {
+    c->rho_iq = iq;
+    c->chi_iq = c->eps_iq = -1;
+    return CHI0_OK;
+  }
+  // ---- device buffers
+  const size_t cb = cplx_bytes(c);
+  const size_t ubytes = (size_t)c->nk * c->nb * g.N1 * g.NZ * g.N2 * cb;
+  if ((s = ensure(c, c->d_U, ubytes, "mixed-grid wavefunctions")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_R, (size_t)c->nt * g.ng * cb, "rho")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_gresp, (size_t)g.ng * 12, "G set")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_kq, (size_t)c->nk * 4, "k pairs")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_g0, (size_t)c->nk * 12, "umklapp")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_tw1, (size_t)g.N1 * cb, "twiddles")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_tw2, (size_t)g.N2 * cb, "twiddles")) != CHI0_OK) return s;
+  CK(cudaMemcpyAsync(c->d_gresp.p, c->h_gresp.data(), (size_t)g.ng * 12, cudaMemcpyHostToDevice, c->st), "G set H2D");
+  CK(cudaMemcpyAsync(c->d_kq.p, c->h_kq.data(), (size_t)c->nk * 4, cudaMemcpyHostToDevice, c->st), "kq H2D");
+  CK(cudaMemcpyAsync(c->d_g0.p, c->h_g0.data(), (size_t)c->nk * 12, cudaMemcpyHostToDevice, c->st), "g0 H2D");
+  cudaError_t e;
+  record(c, 0, true);
+  if (c->fp64) {
+    std::vector<double2> t1, t2;
+    twiddles(g.N1, t1);
+    twiddles(g.N2, t2);
+    CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    e = chi0::launch_wf_to_mixed<double>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
+                                         (const double2*)c->d_coef.p, (const double2*)c->d_tw1.p,
+                                         (const double2*)c->d_tw2.p, (double2*)c->d_U.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    e = chi0::launch_rho_pairs<double, double2>(
+        g, (const double2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+        (const int32_t*)c->d_gresp.p, (const double2*)c->d_tw1.p, (const double2*)c->d_tw2.p,
+        (double2*)c->d_R.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
+  } else {
+    std::vector<double2> t1d, t2d;
+    twiddles(g.N1, t1d);
+    twiddles(g.N2, t2d);
+    std::vector<float2> t1(t1d.size()), t2(t2d.size());
+    for (size_t i = 0; i < t1d.size(); ++i) t1[i] = make_float2((float)t1d[i].x, (float)t1d[i].y);
+    for (size_t i = 0; i < t2d.size(); ++i) t2[i] = make_float2((float)t2d[i].x, (float)t2d[i].y);
+    CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    e = chi0::launch_wf_to_mixed<float>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
+                                        (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
+                                        (const float2*)c->d_tw2.p, (float2*)c->d_U.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    e = chi0::launch_rho_pairs<float, float2>(
+        g, (const float2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+        (const int32_t*)c->d_gresp.p, (const float2*)c->d_tw1.p, (const float2*)c->d_tw2.p,
+        (float2*)c->d_R.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
+  }
+  record(c, 0, false);
+  // algorithmic accounting: coefficients in, rho out; FLOPs of the pruned transforms
+  c->stage_bytes[0] = (double)c->nk * c->nb * c->npw_max * cb + (double)c->nt * g.ng * cb;
+  // executed complex multiply-adds per transition: per x plane the z correlation
+  // (N2 HZ NZ), the pruned y transform (HY HZ N2) and the x accumulation (ng)
+  c->stage_flops[0] = 8.0 * (double)c->nt * g.N1 *
+                      ((double)g.N2 * g.HZ * g.NZ + (double)g.HY * g.HZ * g.N2 + (double)g.ng);
+  c->rho_iq = iq;
+  c->chi_iq = c->eps_iq = -1;
+  return CHI0_OK;
+}
+
+chi0_status chi0_build_chi0(chi0_ctx* c, int iq, void* out, int out_on_device) {
+  if (!c) return CHI0_EINVAL;
+  if (iq != c->rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  for (int iw = 0; iw < nw; ++iw)
+    if (c->om[2 * iw] != 0.0)
+      return fail(c, CHI0_EUNSUPPORTED, "frequency %d has a real part: non-Hermitian chi0 not supported", iw);
+  chi0_status s;
+  const size_t n2 = (size_t)ng * ng;
+  if ((s = ensure(c, c->d_chi, n2 * nw * 16, "chi0")) != CHI0_OK) return s;
+  if (!c->d_err.p) {
+    if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
+    CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
+  }
+  if (c->nt == 0) {
+    CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw * 16, c->st), "zero chi0");
+  } else {
+    if ((s = ensure(c, c->d_w, (size_t)c->nt * nw * 8, "weights")) != CHI0_OK) return s;
+    if ((s = ensure(c, c->d_omim, (size_t)nw * 8, "frequencies")) != CHI0_OK) return s;
+    std::vector<double> omim(nw);
+    for (int iw = 0; iw < nw; ++iw) omim[iw] = c->om[2 * iw + 1];
+    CK(cudaMemcpyAsync(c->d_omim.p, omim.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
+    record(c, 1, true);
+    cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
+                                         (const double*)c->d_eps.p, (const double*)c->d_occ.p,
+                                         (const double*)c->d_omim.p, nullptr, nw, c->cfg.eta, pref,
+                                         c->cfg.occ_drop_tol, (double*)c->d_w.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
+    if (c->fp64) {
+      // split the transitions into chunks so that the grid fills the GPU
+      const int nT = (ng + 31) / 32;
+      const int64_t tiles = (int64_t)nT * (nT + 1) / 2 * nw;
+      int64_t want = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
+      const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(8ull << 30) / (int64_t)(n2 * nw * 16));
+      want = std::min<int64_t>({want, mem_cap, (c->nt + 63) / 64});
+      c->nchunks = (int)std::max<int64_t>(1, want);
+      c->kchunk = (int)((c->nt + c->nchunks - 1) / c->nchunks);
+      if ((s = ensure(c, c->d_part, n2 * nw * c->nchunks * 16, "chi0 partials")) != CHI0_OK) return s;
+      e = chi0::launch_chi0_fp64_partials((const double2*)c->d_R.p, (const double*)c->d_w.p, c->nt, ng,
+                                          nw, c->kchunk, c->nchunks, (double2*)c->d_part.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "chi0 fp64 launch");
+      record(c, 1, false);
+      record(c, 2, true);
+      e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw,
+                                   (double2*)c->d_chi.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch");
+      record(c, 2, false);
+    } else {
+      record(c, 1, false);
+      s = chi0::tc_build_chi0(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p);
+      if (s != CHI0_OK) return s;
+    }
+    c->stage_flops[1] = 4.0 * (double)ng * (ng + 1) * (double)c->nt * nw;
+    c->stage_bytes[1] = (double)c->nt * ng * cplx_bytes(c) + (double)n2 * nw * 16;
+  }
+  c->chi_iq = iq;
+  c->eps_iq = -1;
+  if (out) {
+    CK(cudaMemcpyAsync(out, c->d_chi.p, n2 * nw * 16,
+                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st),
+       "chi0 copy out");
+    if (!out_on_device) {
+      CK(cudaStreamSynchronize(c->st), "synchronize");
+      return check_device_error(c);
+    }
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_invert_eps(chi0_ctx* c, int iq, void* out, int out_on_device) {
+  if (!c) return CHI0_EINVAL;
+  if (iq != c->chi_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_build_chi0(%d) must come first", iq);
+  if (!out) return fail(c, CHI0_EINVAL, "NULL output");
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  const size_t n2 = (size_t)ng * ng;
+  chi0_status s;
+  if ((s = ensure(c, c->d_vsqrt, (size_t)ng * 8, "coulomb")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_colp, (size_t)nw * ng * 32 * 16, "panels")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_rowp, (size_t)nw * ng * 32 * 16, "panels")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_pinv, (size_t)nw * 32 * 32 * 16, "pivot blocks")) != CHI0_OK) return s;
+  double2* A;
+  if (out_on_device) {
+    A = (double2*)out;
+  } else {
+    if ((s = ensure(c, c->d_A, n2 * nw * 16, "eps")) != CHI0_OK) return s;
+    A = (double2*)c->d_A.p;
+  }
+  std::vector<double> v(ng);
+  int64_t qi[3];
+  q_integers(c, iq, qi);
+  for (int i = 0; i < ng; ++i) {
+    double q2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double comp = (double)qi[d] / c->cfg.kgrid[d] + c->h_gresp[3 * i + d];
+      q2 += comp * comp;
+    }
+    const double qg = (2.0 * M_PI / c->a) * std::sqrt(q2);
+    if (qg == 0.0) return fail(c, CHI0_EINVAL, "|q+G| = 0: bare Coulomb interaction diverges");
+    v[i] = std::sqrt(4.0 * M_PI) / qg;
+  }
+  CK(cudaMemcpyAsync(c->d_vsqrt.p, v.data(), ng * 8, cudaMemcpyHostToDevice, c->st), "v H2D");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  record(c, 3, true);
+  cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p, (const double*)c->d_vsqrt.p, ng, nw, A,
+                                     (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
+                                     (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
+  record(c, 3, false);
+  c->stage_flops[3] = 8.0 * (double)ng * ng * ng * nw;
+  c->stage_bytes[3] = 2.0 * (double)n2 * nw * 16;
+  c->eps_iq = iq;
+  if (!out_on_device) {
+    CK(cudaMemcpyAsync(out, A, n2 * nw * 16, cudaMemcpyDeviceToHost, c->st), "eps copy out");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    return check_device_error(c);
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_get_response_gvectors(chi0_ctx* c, int iq, int32_t* out) {
+  if (!c) return CHI0_EINVAL;
+  if (iq < 0 || iq >= c->cfg.nq || !out) return fail(c, CHI0_EINVAL, "bad iq or NULL out");
+  std::vector<int32_t> g;
+  response_set(c, iq, g);
+  std::memcpy(out, g.data(), g.size() * 4);
+  return CHI0_OK;
+}
+
+chi0_status chi0_get_transitions(chi0_ctx* c, int64_t* nt, int32_t* out) {
+  if (!c) return CHI0_EINVAL;
+  if (c->rho_iq < 0) return fail(c, CHI0_ESTATE, "no transitions before chi0_compute_rho");
+  if (nt) *nt = c->nt;
+  if (out) {
+    int64_t t = 0;
+    for (int ik = 0; ik < c->nk; ++ik)
+      for (int n = 0; n < c->Nn; ++n)
+        for (int m = 0; m < c->Nm; ++m, ++t) {
+          out[3 * t] = ik;
+          out[3 * t + 1] = c->n_lo + n;
+          out[3 * t + 2] = m;
+        }
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_get_rho(chi0_ctx* c, void* out) {
+  if (!c) return CHI0_EINVAL;
+  if (c->rho_iq < 0) return fail(c, CHI0_ESTATE, "no rho before chi0_compute_rho");
+  if (!out) return fail(c, CHI0_EINVAL, "NULL out");
+  const size_t n = (size_t)c->nt * c->cfg.ng;
+  if (n == 0) return CHI0_OK;
+  if (c->fp64) {
+    CK(cudaMemcpyAsync(out, c->d_R.p, n * 16, cudaMemcpyDeviceToHost, c->st), "rho D2H");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  } else {
+    std::vector<float2> tmp(n);
+    CK(cudaMemcpyAsync(tmp.data(), c->d_R.p, n * 8, cudaMemcpyDeviceToHost, c->st), "rho D2H");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    double2* o = (double2*)out;
+    for (size_t i = 0; i < n; ++i) o[i] = make_double2(tmp[i].x, tmp[i].y);
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_synchronize(chi0_ctx* c) {
+  if (!c) return CHI0_EINVAL;
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  CK(cudaGetLastError(), "pending error");
+  return check_device_error(c);
+}
+
+chi0_status chi0_get_stats(chi0_ctx* c, double* ms, double* bytes, double* flops) {
+  if (!c) return CHI0_EINVAL;
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  for (int sidx = 0; sidx < 4; ++sidx) {
+    if (c->ev_pending[sidx] && c->ev[2 * sidx] && c->ev[2 * sidx + 1]) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->ev[2 * sidx], c->ev[2 * sidx + 1]) == cudaSuccess)
+        c->stage_ms[sidx] = t;
+      cudaGetLastError();
+      c->ev_pending[sidx] = false;
+    }
+    if (ms) ms[sidx] = c->stage_ms[sidx];
+    if (bytes) bytes[sidx] = c->stage_bytes[sidx];
+    if (flops) flops[sidx] = c->stage_flops[sidx];
+  }
+  return CHI0_OK;
+}
+
+const char* chi0_last_error(const chi0_ctx* c) {
+  if (!c) return "NULL context";
+  return c->err.c_str();
+}
+
+void chi0_destroy(chi0_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  DevBuf* bufs[] = {&c->d_gvec, &c->d_npw, &c->d_coef, &c->d_eps, &c->d_occ, &c->d_stage,
+                    &c->d_gresp, &c->d_kq, &c->d_g0, &c->d_tw1, &c->d_tw2, &c->d_U, &c->d_R,
+                    &c->d_w, &c->d_part, &c->d_chi, &c->d_A, &c->d_colp, &c->d_rowp, &c->d_pinv,
+                    &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc};
+  for (DevBuf* b : bufs) release(*b);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  chi0::tc_release(c);
+  delete c;
+}
+
+}  // extern "C"

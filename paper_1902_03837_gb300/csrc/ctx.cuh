@@ -1,0 +1,67 @@
+// Context of libchi0 shared by its translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/chi0.h"
+#include "internal.cuh"
+
+using chi0::RhoGeom;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct chi0_ctx {
+  chi0_config cfg{};
+  std::vector<double> q;      // [nq][3]
+  std::vector<double> om;     // [nw][2]
+  int nk = 0, nb = 0, npw_max = 0;
+  double a = 0.0, omega_cell = 0.0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  bool fp64 = true;
+
+  // inputs
+  std::vector<int32_t> h_npw;
+  std::vector<int32_t> h_gvec;   // [nk][npw_max][3]
+  std::vector<char> wf_set;
+  std::vector<double> h_eps, h_occ;
+  bool energies_set = false;
+  DevBuf d_gvec, d_npw, d_coef, d_eps, d_occ, d_stage;
+
+  // q-point state
+  int rho_iq = -1, chi_iq = -1, eps_iq = -1;
+  std::vector<int32_t> h_gresp;  // [ng][3] of rho_iq
+  std::vector<int32_t> h_kq, h_g0;
+  int n_lo = 0, Nn = 0, Nm = 0;
+  int64_t nt = 0;
+  RhoGeom geom{};
+  DevBuf d_gresp, d_kq, d_g0, d_tw1, d_tw2, d_U, d_R, d_w, d_part, d_chi, d_A, d_colp, d_rowp,
+      d_pinv, d_err, d_vsqrt, d_omim, d_tc;
+  int nchunks = 1, kchunk = 0;
+
+  // timing
+  cudaEvent_t ev[8] = {};
+  double stage_ms[4] = {0, 0, 0, 0};
+  double stage_bytes[4] = {0, 0, 0, 0};
+  double stage_flops[4] = {0, 0, 0, 0};
+  bool ev_pending[4] = {false, false, false, false};
+};
+
+
+namespace chi0 {
+// record msg on c and return s
+chi0_status ctx_fail(chi0_ctx* c, chi0_status s, const char* msg);
+// grow b to at least bytes (device memory; contents not preserved)
+chi0_status ctx_ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what);
+// split-precision tensor-core contraction (mixed mode): chi[iw][i][j] from
+// R (complex64 [nt][ng]) and real weights w[iw][t]
+chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
+                          double2* chi);
+void tc_release(chi0_ctx* c);
+}  // namespace chi0

@@ -1,0 +1,71 @@
+// Internal declarations shared by the translation units of libchi0.
+// Not part of the public ABI (see include/chi0.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace chi0 {
+
+template <typename T> struct C2;
+template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; };
+
+// Geometry of the oscillator-strength computation for one q point.
+//
+// The real-space grid is (N1, N2, N3) = (x, y, z).  Wavefunctions are held in
+// a mixed representation U_n(x, y, gz): the inverse transform is done along x
+// and y only, z stays in reciprocal space (gz in [-Lz, Lz], NZ = 2 Lz + 1).
+// The response vectors G_i are used through h_i = G_i - G0 (G0: umklapp of
+// the k-pair); hz_rel = G_i,z - Mz_lo in [0, HZ), and likewise for y.
+struct RhoGeom {
+  int N1, N2, N3;
+  int Lx, Ly, Lz;          // largest |G_a| over every wavefunction sphere
+  int NX, NY, NZ;          // 2 L + 1
+  int nk, nb, npw_max;
+  int ng;
+  int Mx_lo, My_lo, Mz_lo; // smallest G_a over the response set
+  int HX, HY, HZ;          // extent of the response set along each axis
+  int n_lo, Nn;            // n bands (at k): [n_lo, n_lo + Nn)
+  int Nm;                  // m bands (at k - q): [0, Nm)
+  int g0max;               // largest |G0_a| over the k-pairs (umklapp)
+};
+
+// ---- launchers (stream-ordered; return cudaGetLastError()) ----
+
+// a1: sphere -> mixed grid U[k][band][x][gz][y] for every k and band.
+template <typename T>
+cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int32_t* npw,
+                               const typename C2<T>::t* coef, const typename C2<T>::t* tw1,
+                               const typename C2<T>::t* tw2, typename C2<T>::t* U,
+                               cudaStream_t s);
+
+// a2: rho for every transition of the dense (k, n, m) block, written to
+// R[t][i], t = ((ik * Nn) + (n - n_lo)) * Nm + m.
+template <typename T, typename TOUT>
+cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
+                             const int32_t* g0, const int32_t* gresp,
+                             const typename C2<T>::t* tw1, const typename C2<T>::t* tw2,
+                             TOUT* R, cudaStream_t s);
+
+// a3: real transition weights w[iw][t] (FP64).
+cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
+                           const double* eps, const double* occ, const double* omega_im,
+                           const double* omega_re, int nw, double eta, double pref,
+                           double occ_tol, double* w, cudaStream_t s);
+
+// a4 (FP64 form): split-K partials of chi0 = sum_t w_t R_t R_t^H, lower
+// triangle tiles; part[kc][iw][i][j] (complex128).
+cudaError_t launch_chi0_fp64_partials(const double2* R, const double* w, int64_t nt, int ng,
+                                      int nw, int kchunk, int nchunks, double2* part,
+                                      cudaStream_t s);
+// Sum of the partials, Hermitian completion: chi[iw][i][j].
+cudaError_t launch_chi0_reduce(const double2* part, int nchunks, int ng, int nw, double2* chi,
+                               cudaStream_t s);
+
+// a5: eps~ = 1 - V chi V, then in-place blocked Gauss-Jordan inverse.
+cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,
+                         double2* colpanel, double2* rowpanel, double2* pinv, int* err_flag,
+                         cudaStream_t s);
+
+}  // namespace chi0

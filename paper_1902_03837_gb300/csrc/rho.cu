@@ -1,0 +1,389 @@
+// Oscillator strengths rho_{nmk}(q,G) = <n k| e^{i(q+G).r} |m k-q>
+// (Linear Response section, Eq. rhotw), through the real-space product of the
+// two states and a Fourier transform, as the paper describes.
+//
+// GB300 design.  With u_n(r) = sum_G c_n(G) e^{iG.r} on the N1 x N2 x N3 grid
+// and h = G - G0 (k - q = k' + G0):
+//
+//   rho(G) = 1/(N1 N2 N3) sum_r conj(u_n(r)) u_m(r) e^{i h.r}.
+//
+// The orbitals are transformed back along x and y only (kernel a1), so along
+// z they stay band-limited spectra U(x, y, gz), gz in [-Lz, Lz].  For one
+// (x, y) column the z part of the product and its forward transform collapse
+// into a short correlation of the two spectra:
+//
+//   sum_z conj(u_n) u_m e^{2 pi i hz z / N3} = N3 sum_b conj(U_n(b + hz)) U_m(b),
+//
+// (exact while |b + hz - b'| < N3, i.e. on any alias-free grid), which costs
+// NZ multiply-adds per output instead of an N3-point transform.  The y and x
+// transforms of the product are then pruned DFTs onto the response set only
+// (kernel a2, stages Y and X).  A thread block owns one k-pair, one n band
+// and JM m bands, streams the x planes of the two mixed grids through shared
+// memory and accumulates rho for all its transitions in registers, so the
+// large intermediate of a staged FFT never reaches HBM.
+#include "internal.cuh"
+
+namespace chi0 {
+
+namespace {
+
+template <typename T2>
+__device__ __forceinline__ void cmac(T2& acc, const T2 a, const T2 b) {  // acc += a * b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+template <typename T2>
+__device__ __forceinline__ void cjmac(T2& acc, const T2 a, const T2 b) {  // acc += conj(a) * b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+template <typename T2>
+__device__ __forceinline__ T2 czero() {
+  T2 z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+
+__device__ __forceinline__ int pmod(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// a1: c_{nk}(G) on the k sphere -> U[k][band][x][gz][y]
+//     U(x, y, gz) = sum_{gx, gy} c(gx, gy, gz) e^{2 pi i (gx x / N1 + gy y / N2)}
+// One block per (k, band); the sphere is scattered into a (NZ, NX, NY) box in
+// shared memory, then each gz plane is transformed along y and then x.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_wf_to_mixed(RhoGeom g, const int32_t* __restrict__ gvec, const int32_t* __restrict__ npw,
+              const typename C2<T>::t* __restrict__ coef, const typename C2<T>::t* __restrict__ tw1,
+              const typename C2<T>::t* __restrict__ tw2, typename C2<T>::t* __restrict__ U) {
+  using T2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* box = reinterpret_cast<T2*>(smem_raw);  // [NZ][NX][NY]
+  T2* t1 = box + g.NZ * g.NX * g.NY;          // [NX][N2]
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ik = blockIdx.x / g.nb;
+  const int band = blockIdx.x - ik * g.nb;
+  const int nbox = g.NZ * g.NX * g.NY;
+  for (int i = tid; i < nbox; i += nth) box[i] = czero<T2>();
+  __syncthreads();
+  const int np = npw[ik];
+  const int32_t* gv = gvec + (size_t)ik * g.npw_max * 3;
+  const T2* c = coef + ((size_t)ik * g.nb + band) * g.npw_max;
+  for (int p = tid; p < np; p += nth) {
+    const int gx = gv[3 * p], gy = gv[3 * p + 1], gz = gv[3 * p + 2];
+    box[((gz + g.Lz) * g.NX + (gx + g.Lx)) * g.NY + (gy + g.Ly)] = c[p];
+  }
+  __syncthreads();
+  T2* out = U + ((size_t)ik * g.nb + band) * ((size_t)g.N1 * g.NZ * g.N2);
+  for (int zz = 0; zz < g.NZ; ++zz) {
+    const T2* bz = box + zz * g.NX * g.NY;
+    for (int it = tid; it < g.NX * g.N2; it += nth) {
+      const int gxr = it / g.N2, y = it - gxr * g.N2;
+      int idx = pmod(-g.Ly * y, g.N2);
+      T2 acc = czero<T2>();
+      for (int gyr = 0; gyr < g.NY; ++gyr) {
+        cmac(acc, bz[gxr * g.NY + gyr], tw2[idx]);
+        idx += y;
+        if (idx >= g.N2) idx -= g.N2;
+      }
+      t1[gxr * g.N2 + y] = acc;
+    }
+    __syncthreads();
+    for (int it = tid; it < g.N1 * g.N2; it += nth) {
+      const int x = it / g.N2, y = it - x * g.N2;
+      int idx = pmod(-g.Lx * x, g.N1);
+      T2 acc = czero<T2>();
+      for (int gxr = 0; gxr < g.NX; ++gxr) {
+        cmac(acc, t1[gxr * g.N2 + y], tw1[idx]);
+        idx += x;
+        if (idx >= g.N1) idx -= g.N1;
+      }
+      out[((size_t)x * g.NZ + zz) * g.N2 + y] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2: rho for JM transitions (one n at k, JM consecutive m at k - q).
+// ---------------------------------------------------------------------------
+constexpr int kRhoThreads = 256;
+constexpr int kAccMax = 16;   // register accumulators per thread
+constexpr int kHZT = 4;       // hz outputs per stage-Z work item
+constexpr int kHYT = 4;       // hy outputs per stage-Y work item
+constexpr int kHZY = 2;       // hz columns per stage-Y work item
+
+struct RhoSmem {
+  int padz;      // zero rows below the n plane (and padz + kHZT above)
+  int unp_rows;  // NZ + 2 padz + kHZT
+};
+
+template <typename T2, typename TOUT>
+__device__ __forceinline__ void store_out(TOUT* p, const T2 v, double scale);
+template <>
+__device__ __forceinline__ void store_out<double2, double2>(double2* p, const double2 v, double s) {
+  *p = make_double2(v.x * s, v.y * s);
+}
+template <>
+__device__ __forceinline__ void store_out<float2, float2>(float2* p, const float2 v, double s) {
+  *p = make_float2((float)(v.x * s), (float)(v.y * s));
+}
+
+template <typename T, int JM, typename TOUT>
+__global__ void __launch_bounds__(kRhoThreads)
+k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
+            const int32_t* __restrict__ kq, const int32_t* __restrict__ g0,
+            const int32_t* __restrict__ gresp, const typename C2<T>::t* __restrict__ tw1,
+            const typename C2<T>::t* __restrict__ tw2, TOUT* __restrict__ R) {
+  using T2 = typename C2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int ik = blockIdx.x;
+  const int nrel = blockIdx.y;
+  const int m0 = blockIdx.z * JM;
+  const int cm = min(JM, g.Nm - m0);
+  const int ikp = kq[ik];
+  const int G0x = g0[3 * ik], G0y = g0[3 * ik + 1], G0z = g0[3 * ik + 2];
+  const int NZ = g.NZ, N2 = g.N2, HZ = g.HZ, HY = g.HY;
+  const size_t plane = (size_t)NZ * N2;
+
+  T2* unp = reinterpret_cast<T2*>(smem_raw);          // [unp_rows][N2]
+  T2* ums = unp + (size_t)sm.unp_rows * N2;            // [JM][NZ][N2]
+  T2* zs = ums + (size_t)JM * plane;                   // [JM][HZ][N2]
+  T2* ys = zs + (size_t)JM * HZ * N2;                  // [JM][HY][HZ]
+  T2* twx = ys + (size_t)JM * HY * HZ;                 // [HX]
+  int* gtab = reinterpret_cast<int*>(twx + g.HX);      // [ng]: (hx_rel << 16) | (hy_rel * HZ + hz_rel)
+
+  for (int i = tid; i < sm.unp_rows * N2; i += kRhoThreads) unp[i] = czero<T2>();
+  for (int i = tid; i < g.ng; i += kRhoThreads) {
+    const int hxr = gresp[3 * i] - g.Mx_lo;
+    const int hyr = gresp[3 * i + 1] - g.My_lo;
+    const int hzr = gresp[3 * i + 2] - g.Mz_lo;
+    gtab[i] = (hxr << 16) | (hyr * HZ + hzr);
+  }
+
+  // register accumulators: entry e <-> (j, i) = divmod(tid + e * threads, ng)
+  T2 acc[kAccMax];
+  int ent_j[kAccMax], ent_i[kAccMax];
+#pragma unroll
+  for (int e = 0; e < kAccMax; ++e) {
+    acc[e] = czero<T2>();
+    const int idx = tid + e * kRhoThreads;
+    ent_j[e] = idx / g.ng;
+    ent_i[e] = idx - ent_j[e] * g.ng;
+  }
+
+  const T2* Un = U + ((size_t)ik * g.nb + (g.n_lo + nrel)) * ((size_t)g.N1 * plane);
+  const T2* Um = U + ((size_t)ikp * g.nb + m0) * ((size_t)g.N1 * plane);
+  const size_t band_stride = (size_t)g.N1 * plane;
+  const int hz_base = g.Mz_lo - G0z;  // hz of hz_rel = 0
+  const int hy_base = g.My_lo - G0y;
+  const int hx_base = g.Mx_lo - G0x;
+  const int nhb = (HZ + kHZT - 1) / kHZT;
+  const int nyb = (HY + kHYT - 1) / kHYT;
+  const int nzb = (HZ + kHZY - 1) / kHZY;
+  __syncthreads();
+
+  for (int x = 0; x < g.N1; ++x) {
+    // ---- load the x plane of the n band (into the padded rows) and of the m bands
+    {
+      const T2* src = Un + (size_t)x * plane;
+      T2* dst = unp + (size_t)sm.padz * N2;
+      for (int i = tid; i < (int)plane; i += kRhoThreads) dst[i] = src[i];
+      for (int j = 0; j < cm; ++j) {
+        const T2* s2 = Um + (size_t)j * band_stride + (size_t)x * plane;
+        T2* d2 = ums + (size_t)j * plane;
+        for (int i = tid; i < (int)plane; i += kRhoThreads) d2[i] = s2[i];
+      }
+      for (int i = tid; i < g.HX; i += kRhoThreads) {
+        const int idx = pmod((hx_base + i) * x, g.N1);
+        twx[i] = tw1[idx];
+      }
+    }
+    __syncthreads();
+
+    // ---- stage Z: zs[j][hz][y] = sum_b conj(U_n(y, b + hz)) U_m,j(y, b)
+    for (int it = tid; it < N2 * nhb; it += kRhoThreads) {
+      const int hb = it / N2, y = it - hb * N2;
+      T2 a[JM][kHZT];
+#pragma unroll
+      for (int j = 0; j < JM; ++j)
+#pragma unroll
+        for (int h = 0; h < kHZT; ++h) a[j][h] = czero<T2>();
+      // row of U_n(b + hz) in the padded array: b + hz + Lz + padz (b from -Lz)
+      const T2* un0 = unp + (size_t)(sm.padz + hz_base + hb * kHZT) * N2 + y;
+      for (int b = 0; b < NZ; ++b) {
+        T2 um[JM], un[kHZT];
+#pragma unroll
+        for (int j = 0; j < JM; ++j) um[j] = (j < cm) ? ums[((size_t)j * NZ + b) * N2 + y] : czero<T2>();
+#pragma unroll
+        for (int h = 0; h < kHZT; ++h) un[h] = un0[(size_t)(b + h) * N2];
+#pragma unroll
+        for (int j = 0; j < JM; ++j)
+#pragma unroll
+          for (int h = 0; h < kHZT; ++h) cjmac(a[j][h], un[h], um[j]);
+      }
+#pragma unroll
+      for (int h = 0; h < kHZT; ++h) {
+        const int hzr = hb * kHZT + h;
+        if (hzr < HZ) {
+#pragma unroll
+          for (int j = 0; j < JM; ++j)
+            if (j < cm) zs[((size_t)j * HZ + hzr) * N2 + y] = a[j][h];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- stage Y: ys[j][hy][hz] = sum_y e^{2 pi i hy y / N2} zs[j][hz][y]
+    for (int it = tid; it < cm * nyb * nzb; it += kRhoThreads) {
+      const int j = it / (nyb * nzb);
+      const int r = it - j * (nyb * nzb);
+      const int yb = r / nzb, zb = r - yb * nzb;
+      T2 a[kHYT][kHZY];
+      int idx[kHYT], step[kHYT];
+#pragma unroll
+      for (int h = 0; h < kHYT; ++h) {
+        step[h] = pmod(hy_base + yb * kHYT + h, N2);
+        idx[h] = 0;
+#pragma unroll
+        for (int z = 0; z < kHZY; ++z) a[h][z] = czero<T2>();
+      }
+      const int hz0 = min(zb * kHZY, HZ - 1);
+      const int hz1 = min(zb * kHZY + 1, HZ - 1);
+      const T2* z0p = zs + ((size_t)j * HZ + hz0) * N2;
+      const T2* z1p = zs + ((size_t)j * HZ + hz1) * N2;
+      for (int y = 0; y < N2; ++y) {
+        const T2 v0 = z0p[y], v1 = z1p[y];
+#pragma unroll
+        for (int h = 0; h < kHYT; ++h) {
+          const T2 t = tw2[idx[h]];
+          cmac(a[h][0], t, v0);
+          cmac(a[h][1], t, v1);
+          idx[h] += step[h];
+          if (idx[h] >= N2) idx[h] -= N2;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < kHYT; ++h) {
+        const int hyr = yb * kHYT + h;
+        if (hyr < HY) {
+          ys[((size_t)j * HY + hyr) * HZ + hz0] = a[h][0];
+          if (zb * kHZY + 1 < HZ) ys[((size_t)j * HY + hyr) * HZ + hz1] = a[h][1];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- stage X: rho(G_i) += e^{2 pi i hx x / N1} ys[j][hy_i][hz_i]
+#pragma unroll
+    for (int e = 0; e < kAccMax; ++e) {
+      if (ent_j[e] < cm) {
+        const int gt = gtab[ent_i[e]];
+        cmac(acc[e], twx[gt >> 16], ys[(size_t)ent_j[e] * HY * HZ + (gt & 0xffff)]);
+      }
+    }
+    __syncthreads();
+  }
+
+  const double scale = 1.0 / ((double)g.N1 * (double)g.N2);
+  const int64_t tbase = ((int64_t)ik * g.Nn + nrel) * g.Nm + m0;
+#pragma unroll
+  for (int e = 0; e < kAccMax; ++e) {
+    if (ent_j[e] < cm) store_out<T2, TOUT>(R + (tbase + ent_j[e]) * g.ng + ent_i[e], acc[e], scale);
+  }
+}
+
+template <typename T>
+size_t rho_smem_bytes(const RhoGeom& g, const RhoSmem& sm, int jm) {
+  using T2 = typename C2<T>::t;
+  size_t n = (size_t)sm.unp_rows * g.N2 + (size_t)jm * g.NZ * g.N2 + (size_t)jm * g.HZ * g.N2 +
+             (size_t)jm * g.HY * g.HZ + g.HX;
+  return n * sizeof(T2) + (size_t)g.ng * sizeof(int);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int32_t* npw,
+                               const typename C2<T>::t* coef, const typename C2<T>::t* tw1,
+                               const typename C2<T>::t* tw2, typename C2<T>::t* U,
+                               cudaStream_t s) {
+  using T2 = typename C2<T>::t;
+  const size_t smem = ((size_t)g.NZ * g.NX * g.NY + (size_t)g.NX * g.N2) * sizeof(T2);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_wf_to_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_wf_to_mixed<T><<<g.nk * g.nb, 256, smem, s>>>(g, gvec, npw, coef, tw1, tw2, U);
+  return cudaGetLastError();
+}
+
+template <typename T, int JM, typename TOUT>
+static cudaError_t launch_rho_jm(const RhoGeom& g, const RhoSmem& sm, size_t smem,
+                                 const typename C2<T>::t* U, const int32_t* kq, const int32_t* g0,
+                                 const int32_t* gresp, const typename C2<T>::t* tw1,
+                                 const typename C2<T>::t* tw2, TOUT* R, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_rho_pairs<T, JM, TOUT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.nk, g.Nn, (g.Nm + JM - 1) / JM);
+  k_rho_pairs<T, JM, TOUT><<<grid, kRhoThreads, smem, s>>>(g, sm, U, kq, g0, gresp, tw1, tw2, R);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TOUT>
+cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
+                             const int32_t* g0, const int32_t* gresp,
+                             const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
+                             cudaStream_t s) {
+  if (g.Nn <= 0 || g.Nm <= 0 || g.nk <= 0) return cudaSuccess;
+  if (g.Nn > 65535 || g.HX >= 32768 || g.HY * g.HZ >= 65536) return cudaErrorInvalidValue;
+  // zero padding below/above the n plane must cover every hz = G_z - G0z
+  RhoSmem sm;
+  // every hz = G_z - G0z (plus the tail of the last hz tile) indexes inside the padding
+  sm.padz = g.HZ + kHZT + abs(g.Mz_lo) + g.g0max + 1;
+  sm.unp_rows = g.NZ + 2 * sm.padz + kHZT;
+  const int cap = kRhoThreads * kAccMax;
+  int jm = 4;
+  while (jm > 1 && jm * g.ng > cap) jm /= 2;
+  if (jm * g.ng > cap) return cudaErrorInvalidValue;  // ng > 4096
+  size_t smem = rho_smem_bytes<T>(g, sm, jm);
+  while (smem > 227 * 1024 && jm > 1) {
+    jm /= 2;
+    smem = rho_smem_bytes<T>(g, sm, jm);
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  switch (jm) {
+    case 4: return launch_rho_jm<T, 4, TOUT>(g, sm, smem, U, kq, g0, gresp, tw1, tw2, R, s);
+    case 2: return launch_rho_jm<T, 2, TOUT>(g, sm, smem, U, kq, g0, gresp, tw1, tw2, R, s);
+    default: return launch_rho_jm<T, 1, TOUT>(g, sm, smem, U, kq, g0, gresp, tw1, tw2, R, s);
+  }
+}
+
+template cudaError_t launch_wf_to_mixed<double>(const RhoGeom&, const int32_t*, const int32_t*,
+                                                const double2*, const double2*, const double2*,
+                                                double2*, cudaStream_t);
+template cudaError_t launch_wf_to_mixed<float>(const RhoGeom&, const int32_t*, const int32_t*,
+                                               const float2*, const float2*, const float2*,
+                                               float2*, cudaStream_t);
+template cudaError_t launch_rho_pairs<double, double2>(const RhoGeom&, const double2*,
+                                                       const int32_t*, const int32_t*,
+                                                       const int32_t*, const double2*,
+                                                       const double2*, double2*, cudaStream_t);
+template cudaError_t launch_rho_pairs<float, float2>(const RhoGeom&, const float2*, const int32_t*,
+                                                     const int32_t*, const int32_t*, const float2*,
+                                                     const float2*, float2*, cudaStream_t);
+
+}  // namespace chi0
