@@ -1,0 +1,318 @@
+"""Benchmark of the chi0 / eps^-1 path on GB300.
+
+One step = the whole path over one synthetic system resident in HBM:
+wavefunctions -> mixed grid, oscillator strengths rho for every transition,
+transition weights, the chi0 contraction for every frequency, and the FP64
+Dyson inversion eps~^-1 for every frequency (chi0_compute_rho +
+chi0_build_chi0 + chi0_invert_eps).
+
+Workload (default): the mixed-precision configuration -- cubic cell a = 10
+bohr, 8x8x8 k grid, 16 occupied + 184 empty bands, ~2000 plane waves per
+state, FFT 48^3, N_G = 1000, q = (1/4, 0, 0), 32 imaginary frequencies on a
+Gauss-Legendre grid in [0, 100] eV, complex64 wavefunctions.
+
+Metric: chi0 build throughput in TFLOP/s of the algorithmic Hermitian count
+4 N_G (N_G + 1) N_T N_w per step (N_T = 1,507,328 transitions), i.e. the
+inverse of the build time; ms_per_step is that build time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = ("precision: a=10 bohr, k 8x8x8, 16+184 bands, ~2000 PW, FFT 48^3, N_G=1000, "
+            "q=(1/4,0,0), 32 imaginary GL frequencies in [0,100] eV, complex64 wavefunctions")
+METRIC = "chi0(q,w) build throughput (algorithmic Hermitian TFLOP/s) incl. rho and FP64 eps^-1"
+
+
+def chi0_flops(ng, nt, nw):
+    return 4.0 * ng * (ng + 1) * nt * nw
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p["bf16_tflops_sustained"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_system():
+    from synth import cfg_precision, make_system
+    return make_system(cfg_precision())
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(system, nks, G):
+    """The CPU oracle on nks k points (all transitions there, all G, all w)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    O.chi0_tr(system, 0, G, system.freqs, system.eta, ks=list(range(nks)))
+    dt = time.perf_counter() - t0
+    nt = nks * 16 * 184
+    return dt, chi0_flops(system.ng, nt, system.freqs.size)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    s = build_system()
+    G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
+    nks = 1
+    vals = []
+    for i in range(args.warmup + args.steps):
+        dt, fl = oracle_sample(s, nks, G)
+        if i >= args.warmup:
+            vals.append((dt, fl))
+    tot_t = sum(v[0] for v in vals)
+    tot_f = sum(v[1] for v in vals)
+    value = tot_f / tot_t / 1e12
+    cores = cpu_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{nks} of 512 k points per step"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 numpy oracle, all transitions of {nks} of 512 k points, "
+                                   f"all 1000 G and 32 frequencies, per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1902_03837_gb300 import chi0 as lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = build_system()
+    ng, nw = s.ng, s.freqs.size
+    ctx = lib.Chi0.for_system(s, precision=lib.CHI0_MIXED_BF16X3, stream=stream.cuda_stream)
+    # inputs resident in HBM (device-to-device set keeps the timed region free of host copies)
+    gv_d = [torch.from_numpy(np.ascontiguousarray(s.gvec[ik, :s.npw[ik]])).to(dev) for ik in range(s.nk)]
+    cf_d = [torch.from_numpy(np.ascontiguousarray(s.coef[ik, :, :s.npw[ik]])).to(dev) for ik in range(s.nk)]
+    for ik in range(s.nk):
+        ctx.set_wavefunctions(ik, gv_d[ik], cf_d[ik])
+    ctx.set_energies(s.eps, s.occ)
+    inv_d = torch.empty((nw, ng, ng), dtype=torch.complex128, device=dev)
+
+    def step():
+        ctx.compute_rho(0)
+        ctx.build_chi0(0, None)
+        ctx.invert_eps(0, inv_d)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.synchronize()
+    nt = ctx.get_transitions().shape[0]
+    ctx.get_stats()  # reset the stage timers
+    _, _, _, l0 = ctx.get_stats()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    ctx.synchronize()
+    st_ms, st_bytes, st_flops, l1 = ctx.get_stats()
+    launches = (l1 - l0)
+    if dist is not None:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    flops_step = chi0_flops(ng, nt, nw)
+    value = world * flops_step / (ms_step * 1e-3) / 1e12
+
+    # ---- end to end: host buffers, copies inside the timed region
+    pin_gv = [torch.from_numpy(np.ascontiguousarray(s.gvec[ik, :s.npw[ik]])).pin_memory() for ik in range(s.nk)]
+    pin_cf = [torch.from_numpy(np.ascontiguousarray(s.coef[ik, :, :s.npw[ik]])).pin_memory() for ik in range(s.nk)]
+    out_h = torch.empty((nw, ng, ng), dtype=torch.complex128).pin_memory()
+    h2d = sum(int(x.numel() * x.element_size()) for x in pin_gv + pin_cf) + 2 * s.eps.nbytes
+    d2h = int(out_h.numel() * out_h.element_size())
+
+    def e2e_step():
+        for ik in range(s.nk):
+            ctx.set_wavefunctions(ik, pin_gv[ik], pin_cf[ik])
+        ctx.set_energies(s.eps, s.occ)
+        ctx.compute_rho(0)
+        ctx.build_chi0(0, None)
+        ctx.invert_eps(0, out_h)   # device -> host copy of the result, synchronises
+
+    e2e_step()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * flops_step / (e2e_ms * 1e-3) / 1e12
+    ctx.get_stats()
+    ctx.close()
+
+    if rank != 0:
+        return
+    pk = peaks()
+    # dominant kernel: the stage with the largest device time
+    dom = max(st_ms, key=lambda k: st_ms[k])
+    per_step_ms = {k: v / args.steps for k, v in st_ms.items()}
+    kinds = {"contract": ("tensor", "TFLOP/s"), "rho": ("alu", "TFLOP/s"), "wf_grid": ("alu", "TFLOP/s"),
+             "dyson": ("alu", "TFLOP/s"), "weights": ("hbm", "GB/s"), "reduce": ("hbm", "GB/s")}
+    bound, unit = kinds[dom]
+    if unit == "GB/s":
+        achieved = st_bytes[dom] / (per_step_ms[dom] * 1e-3) / 1e9
+        peak, psrc = pk["hbm_gbs"], f"HBM copy ({pk['source']})"
+    elif bound == "tensor":
+        achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
+        peak, psrc = pk["bf16_tflops_sustained"], f"BF16 dense sustained ({pk['source']})"
+    else:
+        achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
+        peak, psrc = 75.0, "FP32 FMA 152 SMs x 128 lanes x 2 x ~1.93 GHz (probe-measured 75.0)"
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_transitions": nt, "l2": "inputs larger than L2 (mixed grids 32 GB, rho 12 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "stage_ms_per_step": per_step_ms,
+        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "peak_source": psrc, "traffic": None},
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        import oracle as O
+        G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
+        dt, fl = oracle_sample(s, 1, G)
+        line["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": "FP64 numpy oracle, all 2944 transitions of 1 of 512 k points, "
+                                          "all 1000 G and 32 frequencies", "seconds": dt}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

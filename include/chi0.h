@@ -160,16 +160,33 @@ chi0_status chi0_get_transitions(chi0_ctx* ctx, int64_t* nt, int32_t* out);
  * Errors: CHI0_ESTATE, CHI0_ECUDA. */
 chi0_status chi0_get_rho(chi0_ctx* ctx, void* out);
 
+/* Copy selected rows of R (the last chi0_compute_rho) to a host buffer:
+ * rows[nrows] transition indices (0 <= row < nt), out [nrows][ng] complex128.
+ * Synchronises.  Errors: CHI0_ESTATE, CHI0_EINVAL (row out of range), CHI0_ECUDA. */
+chi0_status chi0_get_rho_rows(chi0_ctx* ctx, const int64_t* rows, int64_t nrows, void* out);
+
 /* Wait for all work queued by this context and report device-side errors
  * (CHI0_ETIMEOUT, CHI0_ENOTPD, CHI0_ECUDA). */
 chi0_status chi0_synchronize(chi0_ctx* ctx);
 
-/* Per-stage device times of the last calls (ms, CUDA events on the context's
- * stream; stage 0 = rho, 1 = weights + contraction, 2 = reduce/finish,
- * 3 = Dyson), their algorithmic bytes and flops.  Any pointer may be NULL.
- * Synchronises. */
-chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms_per_stage /*[4]*/, double* bytes /*[4]*/,
-                           double* flops /*[4]*/);
+/* Stages of the path, for chi0_get_stats. */
+enum {
+  CHI0_STAGE_WF_GRID = 0,    /* wavefunctions to the mixed real/reciprocal grid */
+  CHI0_STAGE_RHO = 1,        /* pair products, pruned transforms -> rho */
+  CHI0_STAGE_WEIGHTS = 2,    /* transition weights (+ operand split in mixed mode) */
+  CHI0_STAGE_CONTRACT = 3,   /* chi0 contraction (FP64 tiles or tensor cores) */
+  CHI0_STAGE_REDUCE = 4,     /* chunk sums, Hermitian completion */
+  CHI0_STAGE_DYSON = 5,      /* eps~ and its inverse */
+  CHI0_NSTAGES = 6
+};
+
+/* Device time of every stage summed over the launches since the previous
+ * chi0_get_stats (ms, CUDA events on the context's stream), the algorithmic
+ * bytes and flops of the most recent instance of each stage, and the number
+ * of kernels this context has launched since chi0_create.  Any pointer may
+ * be NULL; arrays have CHI0_NSTAGES entries.  Synchronises. */
+chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms, double* bytes, double* flops,
+                           int64_t* launches);
 
 /* Text of the last error on ctx (static storage inside ctx; never NULL). */
 const char* chi0_last_error(const chi0_ctx* ctx);

@@ -38,12 +38,11 @@ def transitions_tr(system, iq, occ_tol=0.0):
     ikp, _ = kpair_map(system.spec.kgrid, system.q_frac[iq])
     out = []
     for ik in range(system.nk):
-        jk = ikp[ik]
-        for n in range(system.nb):
-            for m in range(system.nb):
-                if system.occ[jk, m] - system.occ[ik, n] > occ_tol:
-                    out.append((ik, n, m))
-    return np.array(out, dtype=np.int64).reshape(-1, 3)
+        # df[n, m] = f_{m,k-q} - f_{n,k}
+        df = system.occ[ikp[ik]][None, :] - system.occ[ik][:, None]
+        n, m = np.nonzero(df > occ_tol)          # row-major: n, then m
+        out.append(np.stack([np.full(n.size, ik), n, m], axis=1))
+    return np.concatenate(out, axis=0).astype(np.int64).reshape(-1, 3)
 
 
 def weights_tr(system, iq, trans, freqs, eta):
@@ -78,7 +77,8 @@ def chi0_tr(system, iq, Gs, freqs, eta, occ_tol=0.0, ks=None):
         blk = rho_block(system, iq, Gs, ik, ns, ms, shifted=True)
         rho = blk[np.searchsorted(ns, sel[:, 1]), np.searchsorted(ms, sel[:, 2]), :]  # (nt, nG)
         w = weights_tr(system, iq, sel, freqs, eta)                                   # (nw, nt)
-        chi += np.einsum("wt,ti,tj->wij", w, rho, np.conj(rho))
+        for iw in range(freqs.size):   # chi(w) += (w_t rho_t(G_i)) rho_t(G_j)^*
+            chi[iw] += (rho.T * w[iw][None, :]) @ np.conj(rho)
     return chi
 
 

@@ -10,5 +10,5 @@ LIB_PATH = os.path.join(HERE, "libchi0.so")
 
 
 def build(force=False, verbose=False):
-    from .build import build as _build
+    from .buildlib import build as _build
     return _build(force=force, verbose=verbose)

@@ -26,7 +26,7 @@ STATUS = {
 EXPORTS = (
     "chi0_create", "chi0_set_wavefunctions", "chi0_set_energies", "chi0_compute_rho",
     "chi0_build_chi0", "chi0_invert_eps", "chi0_get_response_gvectors", "chi0_get_transitions",
-    "chi0_get_rho", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
+    "chi0_get_rho", "chi0_get_rho_rows", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
 )
 
 
@@ -71,8 +71,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_get_response_gvectors.argtypes = [P, I, P]
     lib.chi0_get_transitions.argtypes = [P, ctypes.POINTER(I64), P]
     lib.chi0_get_rho.argtypes = [P, P]
+    lib.chi0_get_rho_rows.argtypes = [P, P, I64, P]
     lib.chi0_synchronize.argtypes = [P]
-    lib.chi0_get_stats.argtypes = [P, P, P, P]
+    lib.chi0_get_stats.argtypes = [P, P, P, P, ctypes.POINTER(I64)]
     lib.chi0_last_error.argtypes = [P]
     lib.chi0_last_error.restype = ctypes.c_char_p
     lib.chi0_destroy.argtypes = [P]
@@ -212,15 +213,27 @@ class Chi0:
         self._check(_lib.chi0_get_rho(self.h, out.ctypes.data))
         return out
 
+    def get_rho_rows(self, rows):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.zeros((rows.size, self.ng), dtype=np.complex128)
+        self._check(_lib.chi0_get_rho_rows(self.h, rows.ctypes.data, rows.size, out.ctypes.data))
+        return out
+
     def synchronize(self):
         self._check(_lib.chi0_synchronize(self.h))
 
+    STAGES = ("wf_grid", "rho", "weights", "contract", "reduce", "dyson")
+
     def get_stats(self):
-        ms = np.zeros(4)
-        by = np.zeros(4)
-        fl = np.zeros(4)
-        self._check(_lib.chi0_get_stats(self.h, ms.ctypes.data, by.ctypes.data, fl.ctypes.data))
-        return ms, by, fl
+        """(ms, bytes, flops) per stage (dicts keyed by STAGES) and the kernel count."""
+        ms = np.zeros(6)
+        by = np.zeros(6)
+        fl = np.zeros(6)
+        nl = ctypes.c_int64()
+        self._check(_lib.chi0_get_stats(self.h, ms.ctypes.data, by.ctypes.data, fl.ctypes.data,
+                                        ctypes.byref(nl)))
+        mk = lambda a: dict(zip(self.STAGES, a.tolist()))  # noqa: E731
+        return mk(ms), mk(by), mk(fl), nl.value
 
     # -- convenience: marshal a synthetic system's arrays
     @classmethod

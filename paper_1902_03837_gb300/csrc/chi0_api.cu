@@ -62,6 +62,27 @@ chi0_status ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) {
 }  // namespace
 
 namespace chi0 {
+void stage_begin(chi0_ctx* c, int stage) {
+  auto& st = c->stage[stage];
+  if (st.used + 2 > st.ev.size()) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    st.ev.push_back(a);
+    st.ev.push_back(b);
+  }
+  cudaEventRecord(st.ev[st.used], c->st);
+}
+void stage_end(chi0_ctx* c, int stage, int kernels) {
+  auto& st = c->stage[stage];
+  if (st.used + 2 > st.ev.size()) return;  // begin failed to get events
+  cudaEventRecord(st.ev[st.used + 1], c->st);
+  st.used += 2;
+  st.launches += kernels;
+  c->launches += kernels;
+}
 chi0_status ctx_fail(chi0_ctx* c, chi0_status s, const char* msg) { c->err = msg; return s; }
 chi0_status ctx_ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) { return ensure(c, b, bytes, what); }
 }  // namespace chi0
@@ -151,17 +172,6 @@ void twiddles(int n, std::vector<T2>& out) {
     out[j].x = std::cos(ang);
     out[j].y = std::sin(ang);
   }
-}
-
-void record(chi0_ctx* c, int stage, bool start) {
-  cudaEvent_t& ev = c->ev[2 * stage + (start ? 0 : 1)];
-  if (!ev && cudaEventCreate(&ev) != cudaSuccess) {
-    cudaGetLastError();
-    ev = nullptr;
-    return;
-  }
-  cudaEventRecord(ev, c->st);
-  if (!start) c->ev_pending[stage] = true;
 }
 
 chi0_status check_device_error(chi0_ctx* c) {
@@ -420,7 +430,6 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
   CK(cudaMemcpyAsync(c->d_kq.p, c->h_kq.data(), (size_t)c->nk * 4, cudaMemcpyHostToDevice, c->st), "kq H2D");
   CK(cudaMemcpyAsync(c->d_g0.p, c->h_g0.data(), (size_t)c->nk * 12, cudaMemcpyHostToDevice, c->st), "g0 H2D");
   cudaError_t e;
-  record(c, 0, true);
   if (c->fp64) {
     std::vector<double2> t1, t2;
     twiddles(g.N1, t1);
@@ -428,10 +437,13 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
     CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
     CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
     CK(cudaStreamSynchronize(c->st), "synchronize");
+    chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
     e = chi0::launch_wf_to_mixed<double>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
                                          (const double2*)c->d_coef.p, (const double2*)c->d_tw1.p,
                                          (const double2*)c->d_tw2.p, (double2*)c->d_U.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
+    chi0::stage_begin(c, CHI0_STAGE_RHO);
     e = chi0::launch_rho_pairs<double, double2>(
         g, (const double2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
         (const int32_t*)c->d_gresp.p, (const double2*)c->d_tw1.p, (const double2*)c->d_tw2.p,
@@ -447,23 +459,36 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
     CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
     CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
     CK(cudaStreamSynchronize(c->st), "synchronize");
+    chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
     e = chi0::launch_wf_to_mixed<float>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
                                         (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
                                         (const float2*)c->d_tw2.p, (float2*)c->d_U.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
+    chi0::stage_begin(c, CHI0_STAGE_RHO);
     e = chi0::launch_rho_pairs<float, float2>(
         g, (const float2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
         (const int32_t*)c->d_gresp.p, (const float2*)c->d_tw1.p, (const float2*)c->d_tw2.p,
         (float2*)c->d_R.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
   }
-  record(c, 0, false);
-  // algorithmic accounting: coefficients in, rho out; FLOPs of the pruned transforms
-  c->stage_bytes[0] = (double)c->nk * c->nb * c->npw_max * cb + (double)c->nt * g.ng * cb;
-  // executed complex multiply-adds per transition: per x plane the z correlation
-  // (N2 HZ NZ), the pruned y transform (HY HZ N2) and the x accumulation (ng)
-  c->stage_flops[0] = 8.0 * (double)c->nt * g.N1 *
-                      ((double)g.N2 * g.HZ * g.NZ + (double)g.HY * g.HZ * g.N2 + (double)g.ng);
+  chi0::stage_end(c, CHI0_STAGE_RHO, 1);
+  // mixed grid: coefficients in, U out; transforms along y (NX N2 NY per gz
+  // plane) and x (N1 N2 NX per gz plane)
+  {
+    auto& a1 = c->stage[CHI0_STAGE_WF_GRID];
+    a1.bytes = (double)c->nk * c->nb * ((double)c->npw_max * (cb + 12) + ubytes / ((double)c->nk * c->nb));
+    a1.flops = 8.0 * (double)c->nk * c->nb * g.NZ *
+               ((double)g.NX * g.N2 * g.NY + (double)g.N1 * g.N2 * g.NX);
+    // rho: every transition reads two N1 x NZ x N2 mixed grids and writes ng values;
+    // executed complex multiply-adds per transition and x plane: the z
+    // correlation (N2 HZ NZ), the pruned y transform (HY HZ N2), the x
+    // accumulation (ng)
+    auto& a2 = c->stage[CHI0_STAGE_RHO];
+    a2.bytes = (double)c->nt * g.ng * cb + (double)ubytes;
+    a2.flops = 8.0 * (double)c->nt * g.N1 *
+               ((double)g.N2 * g.HZ * g.NZ + (double)g.HY * g.HZ * g.N2 + (double)g.ng);
+  }
   c->rho_iq = iq;
   c->chi_iq = c->eps_iq = -1;
   return CHI0_OK;
@@ -493,12 +518,20 @@ chi0_status chi0_build_chi0(chi0_ctx* c, int iq, void* out, int out_on_device) {
     CK(cudaMemcpyAsync(c->d_omim.p, omim.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
     CK(cudaStreamSynchronize(c->st), "synchronize");
     const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
-    record(c, 1, true);
+    chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
     cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
                                          (const double*)c->d_eps.p, (const double*)c->d_occ.p,
                                          (const double*)c->d_omim.p, nullptr, nw, c->cfg.eta, pref,
                                          c->cfg.occ_drop_tol, (double*)c->d_w.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
+    chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+    c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
+    c->stage[CHI0_STAGE_WEIGHTS].flops = 6.0 * (double)c->nt * nw;
+    // chi0 algorithmic flops (Hermitian half): 4 ng (ng + 1) nt per frequency
+    c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)c->nt * nw;
+    c->stage[CHI0_STAGE_CONTRACT].bytes = (double)c->nt * ng * cplx_bytes(c) + (double)c->nt * nw * 8;
+    c->stage[CHI0_STAGE_REDUCE].bytes = (double)n2 * nw * 16;
+    c->stage[CHI0_STAGE_REDUCE].flops = 0;
     if (c->fp64) {
       // split the transitions into chunks so that the grid fills the GPU
       const int nT = (ng + 31) / 32;
@@ -509,22 +542,21 @@ chi0_status chi0_build_chi0(chi0_ctx* c, int iq, void* out, int out_on_device) {
       c->nchunks = (int)std::max<int64_t>(1, want);
       c->kchunk = (int)((c->nt + c->nchunks - 1) / c->nchunks);
       if ((s = ensure(c, c->d_part, n2 * nw * c->nchunks * 16, "chi0 partials")) != CHI0_OK) return s;
+      chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
       e = chi0::launch_chi0_fp64_partials((const double2*)c->d_R.p, (const double*)c->d_w.p, c->nt, ng,
                                           nw, c->kchunk, c->nchunks, (double2*)c->d_part.p, c->st);
       if (e != cudaSuccess) return cuda_fail(c, e, "chi0 fp64 launch");
-      record(c, 1, false);
-      record(c, 2, true);
+      chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
+      chi0::stage_begin(c, CHI0_STAGE_REDUCE);
       e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw,
                                    (double2*)c->d_chi.p, c->st);
       if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch");
-      record(c, 2, false);
+      chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+      c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
     } else {
-      record(c, 1, false);
       s = chi0::tc_build_chi0(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p);
       if (s != CHI0_OK) return s;
     }
-    c->stage_flops[1] = 4.0 * (double)ng * (ng + 1) * (double)c->nt * nw;
-    c->stage_bytes[1] = (double)c->nt * ng * cplx_bytes(c) + (double)n2 * nw * 16;
   }
   c->chi_iq = iq;
   c->eps_iq = -1;
@@ -573,14 +605,15 @@ chi0_status chi0_invert_eps(chi0_ctx* c, int iq, void* out, int out_on_device) {
   }
   CK(cudaMemcpyAsync(c->d_vsqrt.p, v.data(), ng * 8, cudaMemcpyHostToDevice, c->st), "v H2D");
   CK(cudaStreamSynchronize(c->st), "synchronize");
-  record(c, 3, true);
+  chi0::stage_begin(c, CHI0_STAGE_DYSON);
   cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p, (const double*)c->d_vsqrt.p, ng, nw, A,
                                      (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
                                      (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
   if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
-  record(c, 3, false);
-  c->stage_flops[3] = 8.0 * (double)ng * ng * ng * nw;
-  c->stage_bytes[3] = 2.0 * (double)n2 * nw * 16;
+  chi0::stage_end(c, CHI0_STAGE_DYSON, 1 + 3 * ((ng + 31) / 32));
+  // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency
+  c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
+  c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
   c->eps_iq = iq;
   if (!out_on_device) {
     CK(cudaMemcpyAsync(out, A, n2 * nw * 16, cudaMemcpyDeviceToHost, c->st), "eps copy out");
@@ -635,6 +668,32 @@ chi0_status chi0_get_rho(chi0_ctx* c, void* out) {
   return CHI0_OK;
 }
 
+chi0_status chi0_get_rho_rows(chi0_ctx* c, const int64_t* rows, int64_t nrows, void* out) {
+  if (!c) return CHI0_EINVAL;
+  if (c->rho_iq < 0) return fail(c, CHI0_ESTATE, "no rho before chi0_compute_rho");
+  if (nrows < 0 || (nrows > 0 && (!rows || !out))) return fail(c, CHI0_EINVAL, "bad rows/out");
+  const int ng = c->cfg.ng;
+  const size_t cb = cplx_bytes(c);
+  std::vector<char> tmp((size_t)ng * cb);
+  double2* o = (double2*)out;
+  for (int64_t r = 0; r < nrows; ++r) {
+    if (rows[r] < 0 || rows[r] >= c->nt) return fail(c, CHI0_EINVAL, "row %lld out of range", (long long)rows[r]);
+    CK(cudaMemcpyAsync(tmp.data(), (const char*)c->d_R.p + (size_t)rows[r] * ng * cb, (size_t)ng * cb,
+                       cudaMemcpyDeviceToHost, c->st),
+       "rho row D2H");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    for (int i = 0; i < ng; ++i) {
+      if (c->fp64) {
+        o[(size_t)r * ng + i] = ((const double2*)tmp.data())[i];
+      } else {
+        const float2 v = ((const float2*)tmp.data())[i];
+        o[(size_t)r * ng + i] = make_double2(v.x, v.y);
+      }
+    }
+  }
+  return CHI0_OK;
+}
+
 chi0_status chi0_synchronize(chi0_ctx* c) {
   if (!c) return CHI0_EINVAL;
   CK(cudaStreamSynchronize(c->st), "synchronize");
@@ -642,21 +701,29 @@ chi0_status chi0_synchronize(chi0_ctx* c) {
   return check_device_error(c);
 }
 
-chi0_status chi0_get_stats(chi0_ctx* c, double* ms, double* bytes, double* flops) {
+chi0_status chi0_get_stats(chi0_ctx* c, double* ms, double* bytes, double* flops,
+                           int64_t* launches) {
   if (!c) return CHI0_EINVAL;
   CK(cudaStreamSynchronize(c->st), "synchronize");
-  for (int sidx = 0; sidx < 4; ++sidx) {
-    if (c->ev_pending[sidx] && c->ev[2 * sidx] && c->ev[2 * sidx + 1]) {
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, c->ev[2 * sidx], c->ev[2 * sidx + 1]) == cudaSuccess)
-        c->stage_ms[sidx] = t;
-      cudaGetLastError();
-      c->ev_pending[sidx] = false;
+  for (int k = 0; k < CHI0_NSTAGES; ++k) {
+    auto& st = c->stage[k];
+    if (st.used) {
+      double tot = 0.0;
+      for (size_t p = 0; p + 1 < st.used; p += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, st.ev[p], st.ev[p + 1]) == cudaSuccess) tot += t;
+        cudaGetLastError();
+      }
+      st.ms = tot;
+      st.used = 0;
+    } else {
+      st.ms = 0.0;
     }
-    if (ms) ms[sidx] = c->stage_ms[sidx];
-    if (bytes) bytes[sidx] = c->stage_bytes[sidx];
-    if (flops) flops[sidx] = c->stage_flops[sidx];
+    if (ms) ms[k] = st.ms;
+    if (bytes) bytes[k] = st.bytes;
+    if (flops) flops[k] = st.flops;
   }
+  if (launches) *launches = c->launches;
   return CHI0_OK;
 }
 
@@ -673,8 +740,9 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_w, &c->d_part, &c->d_chi, &c->d_A, &c->d_colp, &c->d_rowp, &c->d_pinv,
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc};
   for (DevBuf* b : bufs) release(*b);
-  for (auto& e : c->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto& st : c->stage)
+    for (cudaEvent_t e : st.ev)
+      if (e) cudaEventDestroy(e);
   chi0::tc_release(c);
   delete c;
 }

@@ -133,6 +133,7 @@ __global__ void k_chi0_reduce(const double2* __restrict__ part, int nchunks, int
     sy += v.y;
   }
   double2* o = chi + (size_t)iw * n2;
+  if (i == j) sy = 0.0;  // Hermitian: real diagonal
   o[(size_t)i * ng + j] = make_double2(sx, sy);
   if (i != j) o[(size_t)j * ng + i] = make_double2(sx, -sy);
 }

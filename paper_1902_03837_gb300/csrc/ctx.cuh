@@ -44,13 +44,19 @@ struct chi0_ctx {
   DevBuf d_gresp, d_kq, d_g0, d_tw1, d_tw2, d_U, d_R, d_w, d_part, d_chi, d_A, d_colp, d_rowp,
       d_pinv, d_err, d_vsqrt, d_omim, d_tc;
   int nchunks = 1, kchunk = 0;
+  void* tc = nullptr;  // tensor-core path state (tc.cu)
 
-  // timing
-  cudaEvent_t ev[8] = {};
-  double stage_ms[4] = {0, 0, 0, 0};
-  double stage_bytes[4] = {0, 0, 0, 0};
-  double stage_flops[4] = {0, 0, 0, 0};
-  bool ev_pending[4] = {false, false, false, false};
+  // per-stage device time: CUDA event pairs on the context's stream, summed
+  // over every launch of the stage since the last chi0_get_stats
+  struct Stage {
+    std::vector<cudaEvent_t> ev;  // start, stop, start, stop, ...
+    size_t used = 0;              // events recorded since the last readout
+    double ms = 0, bytes = 0, flops = 0;
+    int64_t launches = 0;
+  };
+  Stage stage[CHI0_NSTAGES];
+  int64_t launches = 0;           // kernels launched since chi0_create
+  double tc_issued_flops = 0;     // tensor-core flops issued by the last mixed contraction
 };
 
 
@@ -59,6 +65,9 @@ namespace chi0 {
 chi0_status ctx_fail(chi0_ctx* c, chi0_status s, const char* msg);
 // grow b to at least bytes (device memory; contents not preserved)
 chi0_status ctx_ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what);
+// bracket the kernels of one stage on the context's stream
+void stage_begin(chi0_ctx* c, int stage);
+void stage_end(chi0_ctx* c, int stage, int kernels);
 // split-precision tensor-core contraction (mixed mode): chi[iw][i][j] from
 // R (complex64 [nt][ng]) and real weights w[iw][t]
 chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,

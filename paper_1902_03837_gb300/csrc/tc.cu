@@ -1,13 +1,554 @@
-// Split-precision tensor-core contraction for the mixed mode (placeholder
-// until the tcgen05 kernel lands).
+// Mixed-precision chi0 contraction on the 5th-generation tensor cores
+// (tcgen05 + TMEM + TMA, sm_103a).
+//
+// chi0(w) = sum_t w_t rho_t rho_t^H (Appendix B: frequency factors times
+// frequency-independent rho rho^* products) is a Hermitian rank-K update with
+// K = number of transitions.  It is computed in real arithmetic: with
+// P_t = w_t rho_t and rows m = 2 i + c (c = 0 real, 1 imaginary part),
+//
+//     A[m][t] = P_t(i).c,   B[m][t] = rho_t(i).c,   D = A B^T  (2 N_G x 2 N_G),
+//     Re chi_ij = D[2i][2j] + D[2i+1][2j+1],   Im chi_ij = D[2i+1][2j] - D[2i][2j+1].
+//
+// Precision: each FP32 operand is split into two BF16 numbers, x = hi + lo
+// (hi = bf16(x), lo = bf16(x - hi), together ~16 bits), and
+// D = Ah Bh + Ah Bl + Al Bh (the lo*lo term, <= 2^-16 of a product, is
+// dropped).  The tensor core's FP32 accumulation loses low bits on every
+// addition with a bias (measured: the error grows linearly with the number of
+// accumulated transitions, ~2e-6 relative per 512), so each TMEM accumulation
+// is limited to 128 transitions; the epilogue warps fold those sub-sums into
+// compensated FP32 sums, and the per-CTA partials are added in FP64.  Only the
+// lower-triangle 128 x 128 tiles of D are computed (chi0 is Hermitian).
+//
+// Kernel structure (one CTA = one tile x one range of transitions, 6 warps):
+//   warp 0      TMA producer: Ah, Al, Bh, Bl tiles (128 x 64 BF16, 128-byte
+//               swizzle) into a 3-stage shared-memory ring (mbarrier tx counts)
+//   warp 1      TMEM allocation (2 x 128 columns); one elected thread issues
+//               tcgen05.mma (M = N = 128, K = 16, BF16 -> FP32) into the two
+//               accumulators in turn and tcgen05.commit
+//   warps 2-5   epilogue: tcgen05.ld of a finished 128 x 128 accumulator,
+//               combination of 2 x 2 real blocks into complex entries,
+//               compensated accumulation in registers, final FP64 partial
+// Every mbarrier wait is bounded: on timeout the kernel raises the device
+// error flag (reported as CHI0_ETIMEOUT), skips the remaining work, frees its
+// TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
 #include "ctx.cuh"
 
 namespace chi0 {
 
-chi0_status tc_build_chi0(chi0_ctx* c, const void*, const double*, int64_t, int, int, double2*) {
-  return ctx_fail(c, CHI0_EUNSUPPORTED, "mixed-precision contraction not built yet");
+namespace {
+
+constexpr int kBM = 128;             // tile rows (real), = 64 complex G
+constexpr int kBN = 128;             // tile cols (real)
+constexpr int kBK = 64;              // transitions per pipeline stage (128 bytes of BF16)
+constexpr int kStages = 3;
+constexpr int kSubKB = 2;           // k-blocks per TMEM accumulation (128 transitions)
+constexpr int kTileBytes = kBM * kBK * 2;         // 16 KB per operand tile
+constexpr int kStageBytes = 4 * kTileBytes;       // Ah, Al, Bh, Bl
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kThreads = 192;
+constexpr long long kSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kErrTimeout = 2;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-void tc_release(chi0_ctx*) {}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Gives up after kSpinCycles or when
+// another role has already given up (abort flag in shared memory).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (*(volatile int*)(err + 1)) {  // another CTA already gave up
+      *abort_flag = 1;
+      return false;
+    }
+    if (clock64() - t0 > kSpinCycles) {
+      *abort_flag = 1;
+      atomicExch(err + 1, kErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulator
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile of 128-byte rows written by
+// TMA with 128-byte swizzle; 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading-dimension offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride-dimension offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tri_decode(int tile, int& I, int& J) {
+  int i = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= tile) ++i;
+  while (i * (i + 1) / 2 > tile) --i;
+  I = i;
+  J = tile - i * (i + 1) / 2;
+}
+
+// Compensated accumulation (Neumaier): s + c carries the running sum.
+__device__ __forceinline__ void nsum(float& s, float& c, float x) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
+}
+
+// One CTA = one lower-triangle tile (I, J) x one range of k-blocks.  The MMA
+// thread alternates between two TMEM accumulators, one per sub-chunk of
+// kSubKB k-blocks; the epilogue warps drain a finished sub-chunk (complex
+// combination, compensated FP32 sums held in registers) while the other one
+// fills, so the tensor core's FP32 accumulation never runs longer than
+// kSubKB * 64 transitions.
+__global__ void __launch_bounds__(kThreads, 1)
+k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+              const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
+              int total_kb, int kb_per_split, double2* __restrict__ part, int ntiles,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kStages * kStageBytes);
+  const uint32_t bar_full = smem_u32(bars);                   // [kStages]
+  const uint32_t bar_empty = smem_u32(bars + kStages);        // [kStages]
+  const uint32_t bar_accf = smem_u32(bars + 2 * kStages);     // [2] accumulator full
+  const uint32_t bar_acce = smem_u32(bars + 2 * kStages + 2); // [2] accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x, split = blockIdx.y;
+  if (*(volatile int*)(err + 1)) return;  // an earlier CTA timed out: skip the work
+  int I, J;
+  tri_decode(tile, I, J);
+  const int kb0 = split * kb_per_split;
+  const int kb1 = min(total_kb, kb0 + kb_per_split);
+  const int nkb = max(0, kb1 - kb0);
+  const int nsub = (nkb + kSubKB - 1) / kSubKB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_accf + 8 * b, 1);
+      mbar_init(bar_acce + 8 * b, 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_ah) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_al) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_bh) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_bl) : "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 2 * kBN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      for (int k = 0; k < nkb; ++k) {
+        const int s = k % kStages;
+        const uint32_t ph = (uint32_t)((k / kStages) & 1);
+        if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, err)) break;
+        const uint32_t st = base + s * kStageBytes;
+        mbar_expect_tx(bar_full + 8 * s, kStageBytes);
+        const int kx = (kb0 + k) * kBK;
+        tma_load_2d(st, &tm_ah, kx, I * kBM, bar_full + 8 * s);
+        tma_load_2d(st + kTileBytes, &tm_al, kx, I * kBM, bar_full + 8 * s);
+        tma_load_2d(st + 2 * kTileBytes, &tm_bh, kx, J * kBN, bar_full + 8 * s);
+        tma_load_2d(st + 3 * kTileBytes, &tm_bl, kx, J * kBN, bar_full + 8 * s);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
+      int k = 0;
+      for (int sc = 0; sc < nsub; ++sc) {
+        const int b = sc & 1;
+        if (!mbar_wait(bar_acce + 8 * b, (uint32_t)(((sc >> 1) & 1) ^ 1), abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(b * kBN);
+        const int kend = min(nkb, (sc + 1) * kSubKB);
+        bool ok = true;
+        for (int kk0 = 0; k < kend; ++k, ++kk0) {
+          const int s = k % kStages;
+          const uint32_t ph = (uint32_t)((k / kStages) & 1);
+          if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * kStageBytes;
+          const uint64_t dah = desc_sw128(st);
+          const uint64_t dal = desc_sw128(st + kTileBytes);
+          const uint64_t dbh = desc_sw128(st + 2 * kTileBytes);
+          const uint64_t dbl = desc_sw128(st + 3 * kTileBytes);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 BF16 = 32 bytes along K
+            umma_bf16(acc, dah + off, dbh + off, idesc, (kk0 > 0 || kk > 0) ? 1u : 0u);
+            umma_bf16(acc, dah + off, dbl + off, idesc, 1u);
+            umma_bf16(acc, dal + off, dbh + off, idesc, 1u);
+          }
+          umma_commit(bar_empty + 8 * s);  // stage free once these MMAs have read it
+        }
+        if (!ok) break;
+        umma_commit(bar_accf + 8 * b);     // sub-chunk sum ready in accumulator b
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5 -> TMEM lane quadrants 2, 3, 0, 1)
+    const int q = warp & 3;
+    const bool odd = (lane & 1) != 0;
+    float accs[32][2], accc[32][2];  // compensated sums: [complex entry][re, im]
+#pragma unroll
+    for (int e = 0; e < 32; ++e) accs[e][0] = accs[e][1] = accc[e][0] = accc[e][1] = 0.f;
+    bool ok = true;
+    for (int sc = 0; sc < nsub; ++sc) {
+      const int b = sc & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * b, (uint32_t)((sc >> 1) & 1), abort_flag, err) ? 1 : 0) != 0;
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kBN);
+#pragma unroll
+      for (int cb = 0; cb < kBN / 16; ++cb) {
+        uint32_t v[16];
+        tmem_ld16(acc + (uint32_t)(cb * 16), v);
+        // rows 2i (even lane) and 2i+1 (odd lane); each lane combines 4 of the 8 complex columns
+        float recv[8];
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+          const float send = __uint_as_float(odd ? v[k2] : v[8 + k2]);
+          recv[k2] = __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const float r0c0 = odd ? recv[2 * jj] : __uint_as_float(v[2 * jj]);           // D[2i][2j]
+          const float r0c1 = odd ? recv[2 * jj + 1] : __uint_as_float(v[2 * jj + 1]);   // D[2i][2j+1]
+          const float r1c0 = odd ? __uint_as_float(v[8 + 2 * jj]) : recv[2 * jj];       // D[2i+1][2j]
+          const float r1c1 = odd ? __uint_as_float(v[9 + 2 * jj]) : recv[2 * jj + 1];   // D[2i+1][2j+1]
+          const int e = cb * 4 + jj;
+          nsum(accs[e][0], accc[e][0], r0c0 + r1c1);
+          nsum(accs[e][1], accc[e][1], r1c0 - r0c1);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acce + 8 * b) : "memory");
+    }
+    if (ok) {
+      const int il = (q * 32 + lane) >> 1;  // complex row of the tile
+      double2* out = part + ((size_t)split * ntiles + tile) * (size_t)(kBM / 2) * (kBN / 2) +
+                     (size_t)il * (kBN / 2) + (odd ? 4 : 0);
+#pragma unroll
+      for (int cb = 0; cb < kBN / 16; ++cb)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int e = cb * 4 + jj;
+          out[cb * 8 + jj] = make_double2((double)accs[e][0] + (double)accc[e][0],
+                                          (double)accs[e][1] + (double)accc[e][1]);
+        }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * kBN);
+  }
+}
+
+// hi/lo BF16 split of the K-major real operand: out[m][t], m = 2 i + c,
+// value = (w_t if w else 1) * R[t][i].c; zero outside (nt, ng).
+constexpr int kPT = 64;  // transitions per tile
+constexpr int kPI = 32;  // complex G per tile
+
+__global__ void __launch_bounds__(256)
+k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, int ng, int64_t kpad,
+       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  __shared__ float tile[2 * kPI][kPT + 1];
+  const int64_t t0 = (int64_t)blockIdx.x * kPT;
+  const int i0 = blockIdx.y * kPI;
+  for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
+    const int tl = e / kPI, il = e % kPI;
+    const int64_t t = t0 + tl;
+    const int i = i0 + il;
+    float2 v = make_float2(0.f, 0.f);
+    if (t < nt && i < ng) {
+      v = R[t * ng + i];
+      if (w) {
+        const float s = (float)w[t];
+        v.x *= s;
+        v.y *= s;
+      }
+    }
+    tile[2 * il][tl] = v.x;
+    tile[2 * il + 1][tl] = v.y;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
+    const int ml = e / (kPT / 2), tp = e % (kPT / 2);
+    const float x0 = tile[ml][2 * tp], x1 = tile[ml][2 * tp + 1];
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+    const size_t off = (size_t)(2 * i0 + ml) * kpad + t0 + 2 * tp;
+    *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+    *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+  }
+}
+
+// chi[i][j] (i >= j) = sum over chunks of the partials (FP64), mirrored.
+__global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int ntiles, int ng,
+                            double2* __restrict__ chi) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ng * ng) return;
+  const int i = (int)(e / ng), j = (int)(e % ng);
+  if (i < j) return;
+  const int I = i / (kBM / 2), J = j / (kBN / 2);
+  const int tile = I * (I + 1) / 2 + J;
+  const size_t off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  double sx = 0.0, sy = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const double2 v = part[((size_t)c * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
+    sx += v.x;
+    sy += v.y;
+  }
+  if (i == j) sy = 0.0;  // Hermitian: real diagonal
+  chi[(size_t)i * ng + j] = make_double2(sx, sy);
+  if (i != j) chi[(size_t)j * ng + i] = make_double2(sx, -sy);
+}
+
+struct TcState {
+  DevBuf ah, al, bh, bl, part;
+  int64_t kpad = 0;
+  int mpad = 0;
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* ptr, int64_t kpad, int rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
+                          double2* chi) {
+  if (!c->tc) c->tc = new TcState();
+  TcState& t = *static_cast<TcState*>(c->tc);
+  t.mpad = (2 * ng + kBM - 1) / kBM * kBM;
+  t.kpad = (nt + kBK - 1) / kBK * kBK;
+  const int nT = t.mpad / kBM;
+  const int ntiles = nT * (nT + 1) / 2;
+  const int total_kb = (int)(t.kpad / kBK);
+  // split the transitions so that the grid fills whole waves of one CTA per SM
+  int nsm = 148;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+  }
+  int nsplit = 1;
+  double best = 1e30;
+  for (int sp = 1; sp <= 64; ++sp) {
+    const int kbps = (total_kb + sp - 1) / sp;
+    if (sp > 1 && kbps < 8 * kSubKB) break;  // keep every CTA busy for a while
+    const int ctas = ntiles * sp;
+    const int waves = (ctas + nsm - 1) / nsm;
+    // time ~ waves * work per CTA; prefer fewer partials on ties
+    const double cost = (double)waves * kbps + 4.0 * sp;
+    if (cost < best) {
+      best = cost;
+      nsplit = sp;
+    }
+  }
+  const int kbpc = (total_kb + nsplit - 1) / nsplit;
+  const int nchunks = (total_kb + kbpc - 1) / kbpc;
+  const size_t opb = (size_t)t.mpad * t.kpad * 2;
+  chi0_status s;
+  if ((s = ctx_ensure(c, t.ah, opb, "A hi")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.al, opb, "A lo")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.part, (size_t)nchunks * ntiles * (kBM / 2) * (kBN / 2) * 16,
+                      "chunk partials")) != CHI0_OK)
+    return s;
+  CUtensorMap m_ah, m_al, m_bh, m_bl;
+  if (!make_map(&m_ah, t.ah.p, t.kpad, t.mpad) || !make_map(&m_al, t.al.p, t.kpad, t.mpad) ||
+      !make_map(&m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&m_bl, t.bl.p, t.kpad, t.mpad))
+    return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
+  cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemBytes);
+  if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
+  const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
+  const int64_t n2 = (int64_t)ng * ng;
+  // B = rho (frequency independent)
+  stage_begin(c, CHI0_STAGE_WEIGHTS);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, nullptr, nt, ng, t.kpad,
+                                   (__nv_bfloat16*)t.bh.p, (__nv_bfloat16*)t.bl.p);
+  stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+  for (int iw = 0; iw < nw; ++iw) {
+    stage_begin(c, CHI0_STAGE_WEIGHTS);
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, w + (size_t)iw * nt, nt, ng, t.kpad,
+                                     (__nv_bfloat16*)t.ah.p, (__nv_bfloat16*)t.al.p);
+    stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+    stage_begin(c, CHI0_STAGE_CONTRACT);
+    k_herk_bf16x3<<<dim3(ntiles, nchunks), kThreads, kSmemBytes, c->st>>>(
+        m_ah, m_al, m_bh, m_bl, total_kb, kbpc, (double2*)t.part.p, ntiles, (int*)c->d_err.p);
+    stage_end(c, CHI0_STAGE_CONTRACT, 1);
+    stage_begin(c, CHI0_STAGE_REDUCE);
+    k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
+        (const double2*)t.part.p, nchunks, ntiles, ng, chi + (size_t)iw * n2);
+    stage_end(c, CHI0_STAGE_REDUCE, 1);
+  }
+  // operand split: R read, hi/lo written (B once, A per frequency)
+  c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(nw + 1) * ((double)nt * ng * 8 + 4.0 * t.mpad * t.kpad);
+  // contraction: each launch streams A and B (hi and lo) once and writes its chunk partials
+  c->stage[CHI0_STAGE_CONTRACT].bytes =
+      (double)nw * (8.0 * t.mpad * t.kpad + (double)nchunks * ntiles * (kBM / 2) * (kBN / 2) * 16);
+  c->stage[CHI0_STAGE_REDUCE].bytes = (double)nw * ((double)nchunks * ntiles * (kBM / 2) * (kBN / 2) * 16 + n2 * 16);
+  // tensor-core work actually issued: 3 BF16 products over the lower-triangle tiles
+  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)ntiles * (double)t.kpad * nw;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
+  return CHI0_OK;
+}
+
+void tc_release(chi0_ctx* c) {
+  if (!c->tc) return;
+  TcState* t = static_cast<TcState*>(c->tc);
+  DevBuf* bufs[] = {&t->ah, &t->al, &t->bh, &t->bl, &t->part};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  delete t;
+  c->tc = nullptr;
+}
 
 }  // namespace chi0
