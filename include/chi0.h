@@ -188,6 +188,31 @@ enum {
 chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms, double* bytes, double* flops,
                            int64_t* launches);
 
+/* Allocation-free eps~^-1 for callers that cannot allocate device memory.
+ * The paper has no counterpart: this exists for code whose device memory is
+ * owned by another allocator, that must keep a fixed device footprint once
+ * running, or that is inside a stream capture, where cudaMalloc is not allowed.
+ * It computes the same result as chi0_invert_eps from a chi0 the caller holds:
+ *   chi0:   device pointer, [nw][ng][ng] complex128 (input, not modified);
+ *   v_sqrt: host pointer, [ng] doubles, V_i = sqrt(4 pi) / |q + G_i| (> 0);
+ *   out:    device pointer, [nw][ng][ng] complex128, receives eps~^-1;
+ *   cuda_stream: cudaStream_t (NULL = default stream).
+ * It calls no allocating routine: its scratch (about 2.1 MB: panels for
+ * ng <= 2048, the pivot-block inverse, V and an error flag) is one static
+ * device array that every GPU loading this library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the error flag is cleared at the start of each call), so calls
+ * whose work overlaps on the GPU -- from two streams or two threads -- race
+ * and must not be issued.  The call synchronises the stream before returning.
+ * Errors: CHI0_EINVAL (NULL pointer, ng or nw < 1, V not finite and positive),
+ * CHI0_EUNSUPPORTED (ng > 2048, beyond the static scratch), CHI0_ENOTPD (a
+ * Gauss-Jordan pivot was not positive: eps~ is not Hermitian positive
+ * definite), CHI0_ECUDA. */
+chi0_status chi0_invert_eps_noalloc(const void* chi0, const double* v_sqrt, int ng, int nw,
+                                    void* out, void* cuda_stream);
+
 /* Text of the last error on ctx (static storage inside ctx; never NULL). */
 const char* chi0_last_error(const chi0_ctx* ctx);
 

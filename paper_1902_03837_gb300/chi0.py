@@ -27,6 +27,7 @@ EXPORTS = (
     "chi0_create", "chi0_set_wavefunctions", "chi0_set_energies", "chi0_compute_rho",
     "chi0_build_chi0", "chi0_invert_eps", "chi0_get_response_gvectors", "chi0_get_transitions",
     "chi0_get_rho", "chi0_get_rho_rows", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
+    "chi0_invert_eps_noalloc",
 )
 
 
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_last_error.restype = ctypes.c_char_p
     lib.chi0_destroy.argtypes = [P]
     lib.chi0_destroy.restype = None
+    lib.chi0_invert_eps_noalloc.argtypes = [P, P, I, I, P, P]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy"):
             getattr(lib, name).restype = I
@@ -99,6 +101,22 @@ def _ptr(a):
             raise ValueError("tensor must be contiguous")
         return a.data_ptr(), 1 if a.is_cuda else 0
     raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def invert_eps_noalloc(chi0, v_sqrt, out, stream=None):
+    """chi0_invert_eps_noalloc: eps~^-1 without device allocation.
+    chi0, out: contiguous complex128 CUDA tensors [nw][ng][ng]; v_sqrt: host
+    float64 [ng].  Raises Chi0Error on a non-zero status."""
+    cp, cdev = _ptr(chi0)
+    op, odev = _ptr(out)
+    if not (cdev and odev):
+        raise ValueError("chi0 and out must be device tensors")
+    v = np.ascontiguousarray(v_sqrt, dtype=np.float64)
+    nw, ng = int(chi0.shape[0]), int(chi0.shape[1])
+    st = _lib.chi0_invert_eps_noalloc(cp, v.ctypes.data, ng, nw, op, stream)
+    if st != 0:
+        raise Chi0Error(st, "chi0_invert_eps_noalloc failed")
+    return out
 
 
 class Chi0:
