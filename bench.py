@@ -101,9 +101,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def build_system():
+def build_system(kgrid=None, nw=32):
+    """The precision workload; kgrid / nw override it for smaller profiling runs."""
     from synth import cfg_precision, make_system
-    return make_system(cfg_precision())
+    spec = cfg_precision(nw=nw)
+    if kgrid is not None:
+        spec.kgrid = tuple(kgrid)
+    return make_system(spec)
+
+
+def workload_name(args):
+    if args.kgrid is None and args.nw == 32:
+        return WORKLOAD
+    k = "x".join(str(v) for v in (args.kgrid or (8, 8, 8)))
+    return WORKLOAD.replace("k 8x8x8", f"k {k}").replace("32 imaginary", f"{args.nw} imaginary")
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -121,7 +132,7 @@ def oracle_sample(system, nks, G):
     t0 = time.perf_counter()
     O.chi0_tr(system, 0, G, system.freqs, system.eta, ks=list(range(nks)))
     dt = time.perf_counter() - t0
-    nt = nks * 16 * 184
+    nt = nks * system.spec.n_occ * (system.nb - system.spec.n_occ)
     return dt, chi0_flops(system.ng, nt, system.freqs.size)
 
 
@@ -129,9 +140,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle as O
-    s = build_system()
+    s = build_system(args.kgrid, args.nw)
     G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
-    nks = 1
+    nks = 4
     vals = []
     for i in range(args.warmup + args.steps):
         dt, fl = oracle_sample(s, nks, G)
@@ -145,10 +156,10 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{nks} of 512 k points per step"},
+        "data": "synthetic", "config": {"workload": workload_name(args), "sample": f"{nks} of {s.nk} k points per step"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"FP64 numpy oracle, all transitions of {nks} of 512 k points, "
-                                   f"all 1000 G and 32 frequencies, per step"},
+                         "sample": f"FP64 numpy oracle, all transitions of {nks} of {s.nk} k points, "
+                                   f"all {s.ng} G and {s.freqs.size} frequencies, per step"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -166,7 +177,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    s = build_system()
+    s = build_system(args.kgrid, args.nw)
     ng, nw = s.ng, s.freqs.size
     ctx = lib.Chi0.for_system(s, precision=lib.CHI0_MIXED_BF16X3, stream=stream.cuda_stream)
     # inputs resident in HBM (device-to-device set keeps the timed region free of host copies)
@@ -271,7 +282,7 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_transitions": nt, "l2": "inputs larger than L2 (mixed grids 32 GB, rho 12 GB)",
+        "config": {"workload": workload_name(args), "n_transitions": nt, "l2": "inputs larger than L2 (mixed grids 32 GB, rho 12 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "stage_ms_per_step": per_step_ms,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
@@ -284,10 +295,12 @@ def run_ours(args, rank, world, dist):
     if not args.no_cpu_baseline:
         import oracle as O
         G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
-        dt, fl = oracle_sample(s, 1, G)
+        nks = 4
+        dt, fl = oracle_sample(s, nks, G)
         line["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
-                                "sample": "FP64 numpy oracle, all 2944 transitions of 1 of 512 k points, "
-                                          "all 1000 G and 32 frequencies", "seconds": dt}
+                                "sample": f"FP64 numpy oracle, all {nks * 2944} transitions of {nks} of {s.nk} "
+                                          f"k points, all {s.ng} G and {s.freqs.size} frequencies",
+                                "seconds": dt}
     print(json.dumps(line), flush=True)
 
 
@@ -298,6 +311,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kgrid", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="smaller k grid for profiling runs, e.g. 4,2,2 (default 8,8,8)")
+    ap.add_argument("--nw", type=int, default=32, help="number of imaginary frequencies")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
