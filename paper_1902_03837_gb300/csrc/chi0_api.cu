@@ -402,6 +402,22 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
   int g0max = 0;
   for (int v : c->h_g0) g0max = std::max(g0max, std::abs(v));
   g.g0max = g0max;
+  g.g0z_min = 1 << 30;
+  g.g0z_max = -(1 << 30);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    g.g0z_min = std::min(g.g0z_min, c->h_g0[3 * ik + 2]);
+    g.g0z_max = std::max(g.g0z_max, c->h_g0[3 * ik + 2]);
+  }
+  // response indices in (Gy, Gz, Gx) order
+  c->h_gperm.resize(g.ng);
+  for (int i = 0; i < g.ng; ++i) c->h_gperm[i] = i;
+  std::stable_sort(c->h_gperm.begin(), c->h_gperm.end(), [&](int a, int b) {
+    const int32_t* A = &c->h_gresp[3 * a];
+    const int32_t* B = &c->h_gresp[3 * b];
+    if (A[1] != B[1]) return A[1] < B[1];
+    if (A[2] != B[2]) return A[2] < B[2];
+    return A[0] < B[0];
+  });
   // the real-space product must not alias onto the response set
   for (int d = 0; d < 3; ++d) {
     const int n = c->cfg.fft[d];
@@ -422,12 +438,14 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
   if ((s = ensure(c, c->d_U, ubytes, "mixed-grid wavefunctions")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_R, (size_t)c->nt * g.ng * cb, "rho")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_gresp, (size_t)g.ng * 12, "G set")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_gperm, (size_t)g.ng * 4, "G order")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_kq, (size_t)c->nk * 4, "k pairs")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_g0, (size_t)c->nk * 12, "umklapp")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_tw1, (size_t)g.N1 * cb, "twiddles")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_tw2, (size_t)g.N2 * cb, "twiddles")) != CHI0_OK) return s;
   CK(cudaMemcpyAsync(c->d_gresp.p, c->h_gresp.data(), (size_t)g.ng * 12, cudaMemcpyHostToDevice, c->st), "G set H2D");
   CK(cudaMemcpyAsync(c->d_kq.p, c->h_kq.data(), (size_t)c->nk * 4, cudaMemcpyHostToDevice, c->st), "kq H2D");
+  CK(cudaMemcpyAsync(c->d_gperm.p, c->h_gperm.data(), (size_t)g.ng * 4, cudaMemcpyHostToDevice, c->st), "G order H2D");
   CK(cudaMemcpyAsync(c->d_g0.p, c->h_g0.data(), (size_t)c->nk * 12, cudaMemcpyHostToDevice, c->st), "g0 H2D");
   cudaError_t e;
   if (c->fp64) {
@@ -446,7 +464,7 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
     chi0::stage_begin(c, CHI0_STAGE_RHO);
     e = chi0::launch_rho_pairs<double, double2>(
         g, (const double2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
-        (const int32_t*)c->d_gresp.p, (const double2*)c->d_tw1.p, (const double2*)c->d_tw2.p,
+        (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const double2*)c->d_tw1.p, (const double2*)c->d_tw2.p,
         (double2*)c->d_R.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
   } else {
@@ -468,7 +486,7 @@ chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
     chi0::stage_begin(c, CHI0_STAGE_RHO);
     e = chi0::launch_rho_pairs<float, float2>(
         g, (const float2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
-        (const int32_t*)c->d_gresp.p, (const float2*)c->d_tw1.p, (const float2*)c->d_tw2.p,
+        (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p, (const float2*)c->d_tw2.p,
         (float2*)c->d_R.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
   }
@@ -610,8 +628,9 @@ chi0_status chi0_invert_eps(chi0_ctx* c, int iq, void* out, int out_on_device) {
                                      (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
                                      (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
   if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
-  chi0::stage_end(c, CHI0_STAGE_DYSON, 1 + 3 * ((ng + 31) / 32));
-  // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency
+  chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * ((ng + 31) / 32));
+  // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency (about
+  // half of them executed, the Hermitian lower tiles)
   c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
   c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
   c->eps_iq = iq;
@@ -736,7 +755,7 @@ void chi0_destroy(chi0_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
   DevBuf* bufs[] = {&c->d_gvec, &c->d_npw, &c->d_coef, &c->d_eps, &c->d_occ, &c->d_stage,
-                    &c->d_gresp, &c->d_kq, &c->d_g0, &c->d_tw1, &c->d_tw2, &c->d_U, &c->d_R,
+                    &c->d_gresp, &c->d_gperm, &c->d_kq, &c->d_g0, &c->d_tw1, &c->d_tw2, &c->d_U, &c->d_R,
                     &c->d_w, &c->d_part, &c->d_chi, &c->d_A, &c->d_colp, &c->d_rowp, &c->d_pinv,
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc};
   for (DevBuf* b : bufs) release(*b);

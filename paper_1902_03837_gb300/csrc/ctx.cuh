@@ -38,10 +38,11 @@ struct chi0_ctx {
   int rho_iq = -1, chi_iq = -1, eps_iq = -1;
   std::vector<int32_t> h_gresp;  // [ng][3] of rho_iq
   std::vector<int32_t> h_kq, h_g0;
+  std::vector<int> h_gperm;       // response indices in (Gy, Gz, Gx) order
   int n_lo = 0, Nn = 0, Nm = 0;
   int64_t nt = 0;
   RhoGeom geom{};
-  DevBuf d_gresp, d_kq, d_g0, d_tw1, d_tw2, d_U, d_R, d_w, d_part, d_chi, d_A, d_colp, d_rowp,
+  DevBuf d_gresp, d_gperm, d_kq, d_g0, d_tw1, d_tw2, d_U, d_R, d_w, d_part, d_chi, d_A, d_colp, d_rowp,
       d_pinv, d_err, d_vsqrt, d_omim, d_tc;
   int nchunks = 1, kchunk = 0;
   void* tc = nullptr;  // tensor-core path state (tc.cu)

@@ -13,7 +13,13 @@
 //
 // and after the last block A holds eps~^-1.  Each step is three launches: the
 // pivot-block inverse (one block per matrix), the two panels, and the rank-nb
-// update of the whole matrix.  FP64 throughout.
+// update.  FP64 throughout.
+//
+// Symmetry halves the work: once the rows/columns of a set S have been swept,
+// A_ji = s conj(A_ij) with s = -1 when exactly one of i, j lies in S and +1
+// otherwise.  Only the tiles on and below the diagonal are updated; the
+// panels read entries above the diagonal through that rule, and a final pass
+// copies the conjugate of the lower tiles into the upper ones.
 #include "internal.cuh"
 
 namespace chi0 {
@@ -98,7 +104,10 @@ k_gj_pivot(double2* __restrict__ A, int ng, int b0, int nb, double2* __restrict_
   }
 }
 
-// colpanel[iw][i][k] = A_i,b0+k (all i);  rowpanel[iw][k][j] = sum_l P_kl A_b0+l,j (all j)
+// colpanel[iw][i][k] = A_i,b0+k (all i);  rowpanel[iw][k][j] = sum_l P_kl A_b0+l,j (all j).
+// Entries above the diagonal tiles are not maintained; they follow from the
+// stored ones: A_i,b = -conj(A_b,i) for i < b0 (i swept, b not), and
+// A_b,j = conj(A_j,b) for j beyond the pivot block (neither swept).
 __global__ void k_gj_panels(const double2* __restrict__ A, int ng, int b0, int nb,
                             const double2* __restrict__ pinv, double2* __restrict__ colp,
                             double2* __restrict__ rowp) {
@@ -109,10 +118,19 @@ __global__ void k_gj_panels(const double2* __restrict__ A, int ng, int b0, int n
   if (e >= ng) return;
   double2* cp = colp + (size_t)iw * ng * kNB;
   double2* rp = rowp + (size_t)iw * kNB * ng;
-  for (int k = 0; k < nb; ++k) cp[(size_t)e * kNB + k] = Am[(size_t)e * ng + b0 + k];
-  // row panel for column e
   double2 col[kNB];
-  for (int l = 0; l < nb; ++l) col[l] = Am[(size_t)(b0 + l) * ng + e];
+  for (int k = 0; k < nb; ++k) {
+    double2 v;
+    if (e >= b0) {
+      v = Am[(size_t)e * ng + b0 + k];
+    } else {
+      const double2 u = Am[(size_t)(b0 + k) * ng + e];
+      v = make_double2(-u.x, u.y);
+    }
+    cp[(size_t)e * kNB + k] = v;
+    // base of the row panel: A_b0+k,e
+    col[k] = (e < b0 + nb) ? Am[(size_t)(b0 + k) * ng + e] : make_double2(v.x, -v.y);
+  }
   for (int k = 0; k < nb; ++k) {
     double sx = 0.0, sy = 0.0;
     for (int l = 0; l < nb; ++l) {
@@ -129,8 +147,17 @@ k_gj_update(double2* __restrict__ A, int ng, int b0, int nb, const double2* __re
             const double2* __restrict__ colp, const double2* __restrict__ rowp) {
   __shared__ double2 Cs[kUT][kNB + 1];  // rows i of the tile, k
   __shared__ double2 Rs[kNB][kUT + 1];  // k, columns j of the tile
-  const int iw = blockIdx.z;
-  const int i0 = blockIdx.y * kUT, j0 = blockIdx.x * kUT;
+  const int iw = blockIdx.y;
+  int I, J;  // lower tile: I >= J
+  {
+    const int t = blockIdx.x;
+    int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    I = r;
+    J = t - r * (r + 1) / 2;
+  }
+  const int i0 = I * kUT, j0 = J * kUT;
   double2* Am = A + (size_t)iw * ng * ng;
   const double2* cp = colp + (size_t)iw * ng * kNB;
   const double2* rp = rowp + (size_t)iw * kNB * ng;
@@ -180,6 +207,19 @@ k_gj_update(double2* __restrict__ A, int ng, int b0, int nb, const double2* __re
   }
 }
 
+// upper tiles <- conjugate transpose of the lower tiles
+__global__ void k_gj_mirror(double2* __restrict__ A, int ng) {
+  const int iw = blockIdx.y;
+  double2* Am = A + (size_t)iw * ng * ng;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ng * ng) return;
+  const int i = (int)(e / ng), j = (int)(e % ng);
+  if (i / kUT < j / kUT) {
+    const double2 v = Am[(size_t)j * ng + i];
+    Am[(size_t)i * ng + j] = make_double2(v.x, -v.y);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,
@@ -193,11 +233,12 @@ cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw
     const int nb = min(kNB, ng - b0);
     k_gj_pivot<<<nw, 256, 0, s>>>(A, ng, b0, nb, pinv, err);
     k_gj_panels<<<dim3((ng + 127) / 128, nw), 128, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp);
-    k_gj_update<<<dim3(nt, nt, nw), 256, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp);
+    k_gj_update<<<dim3(nt * (nt + 1) / 2, nw), 256, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  k_gj_mirror<<<dim3((unsigned)(((int64_t)ng * ng + 255) / 256), nw), 256, 0, s>>>(A, ng);
+  return cudaGetLastError();
 }
 
 }  // namespace chi0

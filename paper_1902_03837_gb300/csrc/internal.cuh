@@ -29,6 +29,7 @@ struct RhoGeom {
   int n_lo, Nn;            // n bands (at k): [n_lo, n_lo + Nn)
   int Nm;                  // m bands (at k - q): [0, Nm)
   int g0max;               // largest |G0_a| over the k-pairs (umklapp)
+  int g0z_min, g0z_max;    // range of G0_z over the k-pairs
 };
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
@@ -41,10 +42,11 @@ cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int3
                                cudaStream_t s);
 
 // a2: rho for every transition of the dense (k, n, m) block, written to
-// R[t][i], t = ((ik * Nn) + (n - n_lo)) * Nm + m.
+// R[t][i], t = ((ik * Nn) + (n - n_lo)) * Nm + m.  gperm: the response indices
+// ordered by (Gy, Gz, Gx) (the order in which a block's threads visit them).
 template <typename T, typename TOUT>
 cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
-                             const int32_t* g0, const int32_t* gresp,
+                             const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
                              const typename C2<T>::t* tw1, const typename C2<T>::t* tw2,
                              TOUT* R, cudaStream_t s);
 

@@ -125,8 +125,8 @@ constexpr int kHYT = 4;       // hy outputs per stage-Y work item
 constexpr int kHZY = 2;       // hz columns per stage-Y work item
 
 struct RhoSmem {
-  int padz;      // zero rows below the n plane (and padz + kHZT above)
-  int unp_rows;  // NZ + 2 padz + kHZT
+  int padz;      // zero rows below the n plane
+  int unp_rows;  // rows of the padded n plane (zero outside [padz, padz + NZ))
 };
 
 template <typename T2, typename TOUT>
@@ -144,33 +144,52 @@ template <typename T, int JM, typename TOUT>
 __global__ void __launch_bounds__(kRhoThreads)
 k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
             const int32_t* __restrict__ kq, const int32_t* __restrict__ g0,
-            const int32_t* __restrict__ gresp, const typename C2<T>::t* __restrict__ tw1,
+            const int32_t* __restrict__ gresp, const int32_t* __restrict__ gperm,
+            const typename C2<T>::t* __restrict__ tw1,
             const typename C2<T>::t* __restrict__ tw2, TOUT* __restrict__ R) {
   using T2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
-  const int ik = blockIdx.x;
-  const int nrel = blockIdx.y;
-  const int m0 = blockIdx.z * JM;
+  // block order: m chunk fastest, then n, then the k-pair, so that the blocks
+  // resident at one time share the mixed grids of one k-pair in L2
+  const int nmc = (g.Nm + JM - 1) / JM;
+  const int mc = blockIdx.x % nmc;
+  const int nrel = (blockIdx.x / nmc) % g.Nn;
+  const int ik = blockIdx.x / (nmc * g.Nn);
+  const int m0 = mc * JM;
   const int cm = min(JM, g.Nm - m0);
   const int ikp = kq[ik];
   const int G0x = g0[3 * ik], G0y = g0[3 * ik + 1], G0z = g0[3 * ik + 2];
   const int NZ = g.NZ, N2 = g.N2, HZ = g.HZ, HY = g.HY;
+  const int N2P = N2 + 1;  // padded row of zs: column reads in stage Y hit distinct banks
   const size_t plane = (size_t)NZ * N2;
 
   T2* unp = reinterpret_cast<T2*>(smem_raw);          // [unp_rows][N2]
   T2* ums = unp + (size_t)sm.unp_rows * N2;            // [JM][NZ][N2]
-  T2* zs = ums + (size_t)JM * plane;                   // [JM][HZ][N2]
-  T2* ys = zs + (size_t)JM * HZ * N2;                  // [JM][HY][HZ]
-  T2* twx = ys + (size_t)JM * HY * HZ;                 // [HX]
-  int* gtab = reinterpret_cast<int*>(twx + g.HX);      // [ng]: (hx_rel << 16) | (hy_rel * HZ + hz_rel)
+  T2* zs = ums + (size_t)JM * plane;                   // [JM][HZ][N2P]
+  T2* ys = zs + (size_t)JM * HZ * N2P;                 // [2][JM][HY][HZ] (two halves of y)
+  T2* twx = ys + (size_t)2 * JM * HY * HZ;             // [2][HX] (double buffered)
+  T2* twy = twx + 2 * g.HX;                            // [HY][N2P]: e^{2 pi i hy y / N2}
+  int* gtab = reinterpret_cast<int*>(twy + (size_t)HY * N2P);  // [ng]: (hx_rel << 16) | (hy_rel * HZ + hz_rel)
+  int* gout = gtab + g.ng;                             // [ng]: response index of gtab entry
 
   for (int i = tid; i < sm.unp_rows * N2; i += kRhoThreads) unp[i] = czero<T2>();
+  // stage-X entries visit the response set in ys order (hy, hz, then hx), so
+  // that neighbouring threads read neighbouring ys words; gperm holds that order
   for (int i = tid; i < g.ng; i += kRhoThreads) {
-    const int hxr = gresp[3 * i] - g.Mx_lo;
-    const int hyr = gresp[3 * i + 1] - g.My_lo;
-    const int hzr = gresp[3 * i + 2] - g.Mz_lo;
+    const int p = gperm[i];
+    const int hxr = gresp[3 * p] - g.Mx_lo;
+    const int hyr = gresp[3 * p + 1] - g.My_lo;
+    const int hzr = gresp[3 * p + 2] - g.Mz_lo;
     gtab[i] = (hxr << 16) | (hyr * HZ + hzr);
+    gout[i] = p;
+  }
+  const int hz_base = g.Mz_lo - G0z;  // hz of hz_rel = 0
+  const int hy_base = g.My_lo - G0y;
+  const int hx_base = g.Mx_lo - G0x;
+  for (int i = tid; i < HY * N2; i += kRhoThreads) {
+    const int hyr = i / N2, y = i - hyr * N2;
+    twy[hyr * N2P + y] = tw2[pmod((hy_base + hyr) * y, N2)];
   }
 
   // register accumulators: entry e <-> (j, i) = divmod(tid + e * threads, ng)
@@ -187,15 +206,14 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
   const T2* Un = U + ((size_t)ik * g.nb + (g.n_lo + nrel)) * ((size_t)g.N1 * plane);
   const T2* Um = U + ((size_t)ikp * g.nb + m0) * ((size_t)g.N1 * plane);
   const size_t band_stride = (size_t)g.N1 * plane;
-  const int hz_base = g.Mz_lo - G0z;  // hz of hz_rel = 0
-  const int hy_base = g.My_lo - G0y;
-  const int hx_base = g.Mx_lo - G0x;
   const int nhb = (HZ + kHZT - 1) / kHZT;
   const int nyb = (HY + kHYT - 1) / kHYT;
   const int nzb = (HZ + kHZY - 1) / kHZY;
+  const int yhalf = (N2 + 1) / 2;
   __syncthreads();
 
   for (int x = 0; x < g.N1; ++x) {
+    T2* tx = twx + (x & 1) * g.HX;
     // ---- load the x plane of the n band (into the padded rows) and of the m bands
     {
       const T2* src = Un + (size_t)x * plane;
@@ -206,10 +224,7 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
         T2* d2 = ums + (size_t)j * plane;
         for (int i = tid; i < (int)plane; i += kRhoThreads) d2[i] = s2[i];
       }
-      for (int i = tid; i < g.HX; i += kRhoThreads) {
-        const int idx = pmod((hx_base + i) * x, g.N1);
-        twx[i] = tw1[idx];
-      }
+      for (int i = tid; i < g.HX; i += kRhoThreads) tx[i] = tw1[pmod((hx_base + i) * x, g.N1)];
     }
     __syncthreads();
 
@@ -240,77 +255,84 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
         if (hzr < HZ) {
 #pragma unroll
           for (int j = 0; j < JM; ++j)
-            if (j < cm) zs[((size_t)j * HZ + hzr) * N2 + y] = a[j][h];
+            if (j < cm) zs[((size_t)j * HZ + hzr) * N2P + y] = a[j][h];
         }
       }
     }
     __syncthreads();
 
-    // ---- stage Y: ys[j][hy][hz] = sum_y e^{2 pi i hy y / N2} zs[j][hz][y]
-    for (int it = tid; it < cm * nyb * nzb; it += kRhoThreads) {
-      const int j = it / (nyb * nzb);
-      const int r = it - j * (nyb * nzb);
-      const int yb = r / nzb, zb = r - yb * nzb;
+    // ---- stage Y: ys[half][j][hy][hz] = sum_{y in half} e^{2 pi i hy y / N2} zs[j][hz][y]
+    for (int it = tid; it < 2 * cm * nyb * nzb; it += kRhoThreads) {
+      const int half = it / (cm * nyb * nzb);
+      const int r0 = it - half * (cm * nyb * nzb);
+      const int j = r0 / (nyb * nzb);
+      const int r = r0 - j * (nyb * nzb);
+      const int zb = r / nyb, yb = r - zb * nyb;
       T2 a[kHYT][kHZY];
-      int idx[kHYT], step[kHYT];
 #pragma unroll
-      for (int h = 0; h < kHYT; ++h) {
-        step[h] = pmod(hy_base + yb * kHYT + h, N2);
-        idx[h] = 0;
+      for (int h = 0; h < kHYT; ++h)
 #pragma unroll
         for (int z = 0; z < kHZY; ++z) a[h][z] = czero<T2>();
-      }
       const int hz0 = min(zb * kHZY, HZ - 1);
       const int hz1 = min(zb * kHZY + 1, HZ - 1);
-      const T2* z0p = zs + ((size_t)j * HZ + hz0) * N2;
-      const T2* z1p = zs + ((size_t)j * HZ + hz1) * N2;
-      for (int y = 0; y < N2; ++y) {
+      const T2* z0p = zs + ((size_t)j * HZ + hz0) * N2P;
+      const T2* z1p = zs + ((size_t)j * HZ + hz1) * N2P;
+      const int hy0 = yb * kHYT;
+      const int ylo = half * yhalf, yhi = min(N2, ylo + yhalf);
+      for (int y = ylo; y < yhi; ++y) {
         const T2 v0 = z0p[y], v1 = z1p[y];
 #pragma unroll
         for (int h = 0; h < kHYT; ++h) {
-          const T2 t = tw2[idx[h]];
+          const T2 t = twy[(size_t)min(hy0 + h, HY - 1) * N2P + y];
           cmac(a[h][0], t, v0);
           cmac(a[h][1], t, v1);
-          idx[h] += step[h];
-          if (idx[h] >= N2) idx[h] -= N2;
         }
       }
+      T2* yo = ys + (size_t)half * JM * HY * HZ;
 #pragma unroll
       for (int h = 0; h < kHYT; ++h) {
-        const int hyr = yb * kHYT + h;
+        const int hyr = hy0 + h;
         if (hyr < HY) {
-          ys[((size_t)j * HY + hyr) * HZ + hz0] = a[h][0];
-          if (zb * kHZY + 1 < HZ) ys[((size_t)j * HY + hyr) * HZ + hz1] = a[h][1];
+          yo[((size_t)j * HY + hyr) * HZ + hz0] = a[h][0];
+          if (zb * kHZY + 1 < HZ) yo[((size_t)j * HY + hyr) * HZ + hz1] = a[h][1];
         }
       }
     }
     __syncthreads();
 
-    // ---- stage X: rho(G_i) += e^{2 pi i hx x / N1} ys[j][hy_i][hz_i]
+    // ---- stage X: rho(G_i) += e^{2 pi i hx x / N1} (ys[0] + ys[1])[j][hy_i][hz_i]
+    const T2* ys1 = ys + (size_t)JM * HY * HZ;
 #pragma unroll
     for (int e = 0; e < kAccMax; ++e) {
       if (ent_j[e] < cm) {
         const int gt = gtab[ent_i[e]];
-        cmac(acc[e], twx[gt >> 16], ys[(size_t)ent_j[e] * HY * HZ + (gt & 0xffff)]);
+        const size_t o = (size_t)ent_j[e] * HY * HZ + (gt & 0xffff);
+        T2 v = ys[o];
+        const T2 v1 = ys1[o];
+        v.x += v1.x;
+        v.y += v1.y;
+        cmac(acc[e], tx[gt >> 16], v);
       }
     }
-    __syncthreads();
+    // no barrier here: the next plane's load writes unp, ums and the other twx
+    // buffer, none of which stage X reads; ys is rewritten only after two more
+    // barriers
   }
 
   const double scale = 1.0 / ((double)g.N1 * (double)g.N2);
   const int64_t tbase = ((int64_t)ik * g.Nn + nrel) * g.Nm + m0;
 #pragma unroll
   for (int e = 0; e < kAccMax; ++e) {
-    if (ent_j[e] < cm) store_out<T2, TOUT>(R + (tbase + ent_j[e]) * g.ng + ent_i[e], acc[e], scale);
+    if (ent_j[e] < cm) store_out<T2, TOUT>(R + (tbase + ent_j[e]) * g.ng + gout[ent_i[e]], acc[e], scale);
   }
 }
 
 template <typename T>
 size_t rho_smem_bytes(const RhoGeom& g, const RhoSmem& sm, int jm) {
   using T2 = typename C2<T>::t;
-  size_t n = (size_t)sm.unp_rows * g.N2 + (size_t)jm * g.NZ * g.N2 + (size_t)jm * g.HZ * g.N2 +
-             (size_t)jm * g.HY * g.HZ + g.HX;
-  return n * sizeof(T2) + (size_t)g.ng * sizeof(int);
+  size_t n = (size_t)sm.unp_rows * g.N2 + (size_t)jm * g.NZ * g.N2 + (size_t)jm * g.HZ * (g.N2 + 1) +
+             (size_t)2 * jm * g.HY * g.HZ + 2 * (size_t)g.HX + (size_t)g.HY * (g.N2 + 1);
+  return n * sizeof(T2) + 2 * (size_t)g.ng * sizeof(int);
 }
 
 }  // namespace
@@ -333,28 +355,34 @@ cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int3
 template <typename T, int JM, typename TOUT>
 static cudaError_t launch_rho_jm(const RhoGeom& g, const RhoSmem& sm, size_t smem,
                                  const typename C2<T>::t* U, const int32_t* kq, const int32_t* g0,
-                                 const int32_t* gresp, const typename C2<T>::t* tw1,
+                                 const int32_t* gresp, const int32_t* gperm,
+                                 const typename C2<T>::t* tw1,
                                  const typename C2<T>::t* tw2, TOUT* R, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_rho_pairs<T, JM, TOUT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(g.nk, g.Nn, (g.Nm + JM - 1) / JM);
-  k_rho_pairs<T, JM, TOUT><<<grid, kRhoThreads, smem, s>>>(g, sm, U, kq, g0, gresp, tw1, tw2, R);
+  const int64_t nblocks = (int64_t)g.nk * g.Nn * ((g.Nm + JM - 1) / JM);
+  if (nblocks > 0x7fffffff) return cudaErrorInvalidValue;
+  k_rho_pairs<T, JM, TOUT><<<(unsigned)nblocks, kRhoThreads, smem, s>>>(g, sm, U, kq, g0, gresp, gperm, tw1, tw2, R);
   return cudaGetLastError();
 }
 
 template <typename T, typename TOUT>
 cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
-                             const int32_t* g0, const int32_t* gresp,
+                             const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
                              const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
                              cudaStream_t s) {
   if (g.Nn <= 0 || g.Nm <= 0 || g.nk <= 0) return cudaSuccess;
   if (g.Nn > 65535 || g.HX >= 32768 || g.HY * g.HZ >= 65536) return cudaErrorInvalidValue;
   // zero padding below/above the n plane must cover every hz = G_z - G0z
   RhoSmem sm;
-  // every hz = G_z - G0z (plus the tail of the last hz tile) indexes inside the padding
-  sm.padz = g.HZ + kHZT + abs(g.Mz_lo) + g.g0max + 1;
-  sm.unp_rows = g.NZ + 2 * sm.padz + kHZT;
+  // rows of the zero-padded n plane: row = padz + hz + b, b in [0, NZ), hz over
+  // every tile of every k-pair: [Mz_lo - G0z_max, Mz_lo + nhb * kHZT - 1 - G0z_min]
+  const int nhb = (g.HZ + kHZT - 1) / kHZT;
+  const int hz_min = g.Mz_lo - g.g0z_max;
+  const int hz_max = g.Mz_lo + nhb * kHZT - 1 - g.g0z_min;
+  sm.padz = max(0, -hz_min);
+  sm.unp_rows = max(sm.padz + hz_max + g.NZ, sm.padz + g.NZ);
   const int cap = kRhoThreads * kAccMax;
   int jm = 4;
   while (jm > 1 && jm * g.ng > cap) jm /= 2;
@@ -366,9 +394,9 @@ cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const
   }
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   switch (jm) {
-    case 4: return launch_rho_jm<T, 4, TOUT>(g, sm, smem, U, kq, g0, gresp, tw1, tw2, R, s);
-    case 2: return launch_rho_jm<T, 2, TOUT>(g, sm, smem, U, kq, g0, gresp, tw1, tw2, R, s);
-    default: return launch_rho_jm<T, 1, TOUT>(g, sm, smem, U, kq, g0, gresp, tw1, tw2, R, s);
+    case 4: return launch_rho_jm<T, 4, TOUT>(g, sm, smem, U, kq, g0, gresp, gperm, tw1, tw2, R, s);
+    case 2: return launch_rho_jm<T, 2, TOUT>(g, sm, smem, U, kq, g0, gresp, gperm, tw1, tw2, R, s);
+    default: return launch_rho_jm<T, 1, TOUT>(g, sm, smem, U, kq, g0, gresp, gperm, tw1, tw2, R, s);
   }
 }
 
@@ -380,10 +408,12 @@ template cudaError_t launch_wf_to_mixed<float>(const RhoGeom&, const int32_t*, c
                                                float2*, cudaStream_t);
 template cudaError_t launch_rho_pairs<double, double2>(const RhoGeom&, const double2*,
                                                        const int32_t*, const int32_t*,
-                                                       const int32_t*, const double2*,
-                                                       const double2*, double2*, cudaStream_t);
+                                                       const int32_t*, const int32_t*,
+                                                       const double2*, const double2*, double2*,
+                                                       cudaStream_t);
 template cudaError_t launch_rho_pairs<float, float2>(const RhoGeom&, const float2*, const int32_t*,
-                                                     const int32_t*, const int32_t*, const float2*,
-                                                     const float2*, float2*, cudaStream_t);
+                                                     const int32_t*, const int32_t*, const int32_t*,
+                                                     const float2*, const float2*, float2*,
+                                                     cudaStream_t);
 
 }  // namespace chi0

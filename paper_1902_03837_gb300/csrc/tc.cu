@@ -201,7 +201,7 @@ __device__ __forceinline__ void nsum(float& s, float& c, float x) {
 __global__ void __launch_bounds__(kThreads, 1)
 k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
-              int total_kb, int kb_per_split, double2* __restrict__ part, int ntiles,
+              int total_kb, int kb_per_split, int mpad, double2* __restrict__ part, int ntiles,
               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -258,11 +258,11 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
         if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, err)) break;
         const uint32_t st = base + s * kStageBytes;
         mbar_expect_tx(bar_full + 8 * s, kStageBytes);
-        const int kx = (kb0 + k) * kBK;
-        tma_load_2d(st, &tm_ah, kx, I * kBM, bar_full + 8 * s);
-        tma_load_2d(st + kTileBytes, &tm_al, kx, I * kBM, bar_full + 8 * s);
-        tma_load_2d(st + 2 * kTileBytes, &tm_bh, kx, J * kBN, bar_full + 8 * s);
-        tma_load_2d(st + 3 * kTileBytes, &tm_bl, kx, J * kBN, bar_full + 8 * s);
+        const int row = (kb0 + k) * mpad;  // k-blocked layout: block kb starts at row kb * mpad
+        tma_load_2d(st, &tm_ah, 0, row + I * kBM, bar_full + 8 * s);
+        tma_load_2d(st + kTileBytes, &tm_al, 0, row + I * kBM, bar_full + 8 * s);
+        tma_load_2d(st + 2 * kTileBytes, &tm_bh, 0, row + J * kBN, bar_full + 8 * s);
+        tma_load_2d(st + 3 * kTileBytes, &tm_bl, 0, row + J * kBN, bar_full + 8 * s);
       }
     }
   } else if (warp == 1) {
@@ -365,16 +365,19 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
   }
 }
 
-// hi/lo BF16 split of the K-major real operand: out[m][t], m = 2 i + c,
-// value = (w_t if w else 1) * R[t][i].c; zero outside (nt, ng).
-constexpr int kPT = 64;  // transitions per tile
+// hi/lo BF16 split of the real operand in k-blocked layout: element (m, t),
+// m = 2 i + c, sits at [t / 64][m][t % 64] (each block of 64 transitions holds
+// all rows, 128 bytes per row), so one 128-row TMA box is one contiguous 16 KB
+// chunk.  value = (w_t if w else 1) * R[t][i].c; zero outside (nt, ng).
+constexpr int kPT = 64;  // transitions per tile (= one k-block)
 constexpr int kPI = 32;  // complex G per tile
 
 __global__ void __launch_bounds__(256)
-k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, int ng, int64_t kpad,
+k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, int ng, int mpad,
        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   __shared__ float tile[2 * kPI][kPT + 1];
-  const int64_t t0 = (int64_t)blockIdx.x * kPT;
+  const int64_t kb = blockIdx.x;
+  const int64_t t0 = kb * kPT;
   const int i0 = blockIdx.y * kPI;
   for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
     const int tl = e / kPI, il = e % kPI;
@@ -393,12 +396,13 @@ k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, i
     tile[2 * il + 1][tl] = v.y;
   }
   __syncthreads();
+  const size_t blk = (size_t)kb * mpad * kPT;
   for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
     const int ml = e / (kPT / 2), tp = e % (kPT / 2);
     const float x0 = tile[ml][2 * tp], x1 = tile[ml][2 * tp + 1];
     const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
     const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
-    const size_t off = (size_t)(2 * i0 + ml) * kpad + t0 + 2 * tp;
+    const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
     *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
     *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
   }
@@ -443,11 +447,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, void* ptr, int64_t kpad, int rows) {
+// 2-D map over the k-blocked operand viewed as [nkb * mpad rows][64 BF16]
+bool make_map(CUtensorMap* m, void* ptr, int64_t kpad, int mpad) {
   auto enc = get_encode();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint64_t dims[2] = {(cuuint64_t)kBK, (cuuint64_t)(kpad / kBK) * (cuuint64_t)mpad};
+  cuuint64_t strides[1] = {(cuuint64_t)kBK * 2};
   cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
@@ -508,20 +513,21 @@ chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t n
                                        kSmemBytes);
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
+  if (t.kpad / kPT > 0x7fffffff / t.mpad) return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
   const int64_t n2 = (int64_t)ng * ng;
   // B = rho (frequency independent)
   stage_begin(c, CHI0_STAGE_WEIGHTS);
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, nullptr, nt, ng, t.kpad,
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, nullptr, nt, ng, t.mpad,
                                    (__nv_bfloat16*)t.bh.p, (__nv_bfloat16*)t.bl.p);
   stage_end(c, CHI0_STAGE_WEIGHTS, 1);
   for (int iw = 0; iw < nw; ++iw) {
     stage_begin(c, CHI0_STAGE_WEIGHTS);
-    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, w + (size_t)iw * nt, nt, ng, t.kpad,
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, w + (size_t)iw * nt, nt, ng, t.mpad,
                                      (__nv_bfloat16*)t.ah.p, (__nv_bfloat16*)t.al.p);
     stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     stage_begin(c, CHI0_STAGE_CONTRACT);
     k_herk_bf16x3<<<dim3(ntiles, nchunks), kThreads, kSmemBytes, c->st>>>(
-        m_ah, m_al, m_bh, m_bl, total_kb, kbpc, (double2*)t.part.p, ntiles, (int*)c->d_err.p);
+        m_ah, m_al, m_bh, m_bl, total_kb, kbpc, t.mpad, (double2*)t.part.p, ntiles, (int*)c->d_err.p);
     stage_end(c, CHI0_STAGE_CONTRACT, 1);
     stage_begin(c, CHI0_STAGE_REDUCE);
     k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
