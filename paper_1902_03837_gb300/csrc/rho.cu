@@ -51,6 +51,31 @@ __device__ __forceinline__ T2 czero() {
   return z;
 }
 
+// asynchronous global -> shared copies (bypass registers; many in flight)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+// copy n bytes (a multiple of 8) with cp.async; 16-byte pieces when both ends allow
+__device__ __forceinline__ void async_copy(void* dst, const void* src, int nbytes, int tid, int nth) {
+  if ((((uintptr_t)dst | (uintptr_t)src | (uintptr_t)nbytes) & 15) == 0) {
+    for (int i = tid; i < nbytes / 16; i += nth)
+      cp_async16(static_cast<char*>(dst) + 16 * i, static_cast<const char*>(src) + 16 * i);
+  } else {
+    for (int i = tid; i < nbytes / 8; i += nth)
+      cp_async8(static_cast<char*>(dst) + 8 * i, static_cast<const char*>(src) + 8 * i);
+  }
+}
+
 __device__ __forceinline__ int pmod(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
@@ -120,7 +145,7 @@ k_wf_to_mixed(RhoGeom g, const int32_t* __restrict__ gvec, const int32_t* __rest
 // ---------------------------------------------------------------------------
 constexpr int kRhoThreads = 256;
 constexpr int kAccMax = 16;   // register accumulators per thread
-constexpr int kHZT = 4;       // hz outputs per stage-Z work item
+constexpr int kHZT = 3;       // hz outputs per stage-Z work item
 constexpr int kHYT = 4;       // hy outputs per stage-Y work item
 constexpr int kHZY = 2;       // hz columns per stage-Y work item
 
@@ -212,21 +237,22 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
   const int yhalf = (N2 + 1) / 2;
   __syncthreads();
 
+  // plane loads: the n band into the padded rows, the m bands, and the
+  // x twiddles; issued asynchronously (the next plane's copies overlap stage X)
+  auto issue_plane = [&](int x) {
+    async_copy(unp + (size_t)sm.padz * N2, Un + (size_t)x * plane, (int)(plane * sizeof(T2)), tid,
+               kRhoThreads);
+    for (int j = 0; j < cm; ++j)
+      async_copy(ums + (size_t)j * plane, Um + (size_t)j * band_stride + (size_t)x * plane,
+                 (int)(plane * sizeof(T2)), tid, kRhoThreads);
+  };
+  issue_plane(0);
+  cp_async_wait_all();
+  __syncthreads();
+
   for (int x = 0; x < g.N1; ++x) {
     T2* tx = twx + (x & 1) * g.HX;
-    // ---- load the x plane of the n band (into the padded rows) and of the m bands
-    {
-      const T2* src = Un + (size_t)x * plane;
-      T2* dst = unp + (size_t)sm.padz * N2;
-      for (int i = tid; i < (int)plane; i += kRhoThreads) dst[i] = src[i];
-      for (int j = 0; j < cm; ++j) {
-        const T2* s2 = Um + (size_t)j * band_stride + (size_t)x * plane;
-        T2* d2 = ums + (size_t)j * plane;
-        for (int i = tid; i < (int)plane; i += kRhoThreads) d2[i] = s2[i];
-      }
-      for (int i = tid; i < g.HX; i += kRhoThreads) tx[i] = tw1[pmod((hx_base + i) * x, g.N1)];
-    }
-    __syncthreads();
+    for (int i = tid; i < g.HX; i += kRhoThreads) tx[i] = tw1[pmod((hx_base + i) * x, g.N1)];
 
     // ---- stage Z: zs[j][hz][y] = sum_b conj(U_n(y, b + hz)) U_m,j(y, b)
     for (int it = tid; it < N2 * nhb; it += kRhoThreads) {
@@ -300,6 +326,9 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
     }
     __syncthreads();
 
+    // the planes of x are no longer read: start copying those of x + 1
+    if (x + 1 < g.N1) issue_plane(x + 1);
+
     // ---- stage X: rho(G_i) += e^{2 pi i hx x / N1} (ys[0] + ys[1])[j][hy_i][hz_i]
     const T2* ys1 = ys + (size_t)JM * HY * HZ;
 #pragma unroll
@@ -314,9 +343,8 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
         cmac(acc[e], tx[gt >> 16], v);
       }
     }
-    // no barrier here: the next plane's load writes unp, ums and the other twx
-    // buffer, none of which stage X reads; ys is rewritten only after two more
-    // barriers
+    cp_async_wait_all();
+    __syncthreads();
   }
 
   const double scale = 1.0 / ((double)g.N1 * (double)g.N2);
