@@ -213,6 +213,56 @@ chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms, double* bytes, double* flo
 chi0_status chi0_invert_eps_noalloc(const void* chi0, const double* v_sqrt, int ng, int nw,
                                     void* out, void* cuda_stream);
 
+/* ---- Learned band-sum terminator -------------------------------------------
+ * The paper's X-terminator (Linear Response section, Eq. X_term_def; its
+ * expressions in Appendix C) corrects a band-truncated chi0 by an extra term
+ * Delta chi.  Here Delta chi_GG'(w) is predicted entry by entry by a small
+ * network trained on pairs of truncated and full-band chi0 of the same
+ * systems; the full-band sum stays the reference that judges it.
+ *   features x = (|q+G|/Kn, |q+G'|/Kn, |Im w|/Wn, Re chi0_trunc/c, Im chi0_trunc/c),
+ *   Kn = largest |q+G| of the response set, Wn = largest |Im w|,
+ *   c = mean_G |chi0_trunc,GG(w_0)|; the prediction y (2 values) means
+ *   Delta chi = c (y0 + i y1), Hermitised before it is added.
+ * Network: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3 with
+ * 5 -> 128 -> 128 -> 2; parameters are one FP32 vector [W1(128x5) b1(128)
+ * W2(128x128) b2(128) W3(2x128) b3(2)] (chi0_mlp_nparams() entries, device
+ * memory, row-major).  bf16 = 1 rounds every operand of a matrix product to
+ * BF16 (FP32 accumulation); bf16 = 0 keeps FP32 operands.  All pointers of
+ * the chi0_mlp_* calls are device pointers; the calls are asynchronous on
+ * `stream`.  Errors: CHI0_EINVAL (NULL pointer, non-positive size),
+ * CHI0_ECUDA. */
+int chi0_mlp_nparams(void);
+
+/* Floats of device workspace that chi0_mlp_loss_grad needs for `batch` samples. */
+int64_t chi0_mlp_workspace_floats(int64_t batch);
+
+/* loss = 1/(2 batch) sum_b sum_o (y_bo - t_bo)^2 and grad = d loss / d params
+ * (backpropagation; block partials summed in a fixed order, so repeatable).
+ * x: [batch][5], t: [batch][2], grad: [nparams], loss: one float (may be NULL),
+ * work: chi0_mlp_workspace_floats(batch) floats. */
+chi0_status chi0_mlp_loss_grad(const float* params, const float* x, const float* t, int64_t batch,
+                               int bf16, float* grad, float* loss, float* work, void* stream);
+
+/* One Adam update (step >= 1, bias-corrected moments m, v of n entries). */
+chi0_status chi0_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t n, float lr,
+                          float beta1, float beta2, float eps, int step, void* stream);
+
+/* y[batch][2] = network(x[batch][5]). */
+chi0_status chi0_mlp_predict(const float* params, const float* x, int64_t batch, int bf16, float* y,
+                             void* stream);
+
+/* Features x [nw*ng*ng][5] of a truncated chi0 (device [nw][ng][ng] c128) at
+ * q index iq, and, when chi_full is not NULL, the targets t [nw*ng*ng][2] =
+ * (chi_full - chi_trunc)/c; *scale receives c (host, may be NULL; reading it
+ * synchronises).  Requires chi0_compute_rho(iq) on ctx (the response set).
+ * Errors: CHI0_EINVAL, CHI0_ESTATE, CHI0_ENOMEM, CHI0_ECUDA. */
+chi0_status chi0_term_features(chi0_ctx* ctx, int iq, const void* chi_trunc, const void* chi_full,
+                               float* x, float* t, double* scale);
+
+/* Use the network `params` (device, nparams floats, kept alive by the caller)
+ * to correct every following chi0_build_chi0 on ctx; NULL switches it off. */
+chi0_status chi0_set_terminator(chi0_ctx* ctx, const float* params, int bf16);
+
 /* Text of the last error on ctx (static storage inside ctx; never NULL). */
 const char* chi0_last_error(const chi0_ctx* ctx);
 

@@ -27,7 +27,8 @@ EXPORTS = (
     "chi0_create", "chi0_set_wavefunctions", "chi0_set_energies", "chi0_compute_rho",
     "chi0_build_chi0", "chi0_invert_eps", "chi0_get_response_gvectors", "chi0_get_transitions",
     "chi0_get_rho", "chi0_get_rho_rows", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
-    "chi0_invert_eps_noalloc",
+    "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
+    "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator",
 )
 
 
@@ -80,9 +81,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_destroy.argtypes = [P]
     lib.chi0_destroy.restype = None
     lib.chi0_invert_eps_noalloc.argtypes = [P, P, I, I, P, P]
+    F = ctypes.c_float
+    lib.chi0_mlp_nparams.argtypes = []
+    lib.chi0_mlp_workspace_floats.argtypes = [I64]
+    lib.chi0_mlp_loss_grad.argtypes = [P, P, P, I64, I, P, P, P, P]
+    lib.chi0_mlp_adam.argtypes = [P, P, P, P, I64, F, F, F, F, I, P]
+    lib.chi0_mlp_predict.argtypes = [P, P, I64, I, P, P]
+    lib.chi0_term_features.argtypes = [P, I, P, P, P, P, P]
+    lib.chi0_set_terminator.argtypes = [P, P, I]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy"):
             getattr(lib, name).restype = I
+    lib.chi0_mlp_workspace_floats.restype = I64
     del D
     return lib
 
@@ -117,6 +127,43 @@ def invert_eps_noalloc(chi0, v_sqrt, out, stream=None):
     if st != 0:
         raise Chi0Error(st, "chi0_invert_eps_noalloc failed")
     return out
+
+
+# ---- learned terminator network (device tensors: float32, contiguous)
+
+def mlp_nparams():
+    return int(_lib.chi0_mlp_nparams())
+
+
+def mlp_workspace_floats(batch):
+    return int(_lib.chi0_mlp_workspace_floats(int(batch)))
+
+
+def _dev(t):
+    p, dev = _ptr(t)
+    if not dev:
+        raise ValueError("device tensor expected")
+    return p
+
+
+def mlp_loss_grad(params, x, t, grad, loss, work, bf16=True, stream=None):
+    st = _lib.chi0_mlp_loss_grad(_dev(params), _dev(x), _dev(t), int(x.shape[0]), int(bool(bf16)),
+                                 _dev(grad), _dev(loss) if loss is not None else None, _dev(work), stream)
+    if st != 0:
+        raise Chi0Error(st, "chi0_mlp_loss_grad failed")
+
+
+def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    st = _lib.chi0_mlp_adam(_dev(params), _dev(grad), _dev(m), _dev(v), int(params.numel()), float(lr),
+                            float(beta1), float(beta2), float(eps), int(step), stream)
+    if st != 0:
+        raise Chi0Error(st, "chi0_mlp_adam failed")
+
+
+def mlp_predict(params, x, y, bf16=True, stream=None):
+    st = _lib.chi0_mlp_predict(_dev(params), _dev(x), int(x.shape[0]), int(bool(bf16)), _dev(y), stream)
+    if st != 0:
+        raise Chi0Error(st, "chi0_mlp_predict failed")
 
 
 class Chi0:
@@ -239,6 +286,18 @@ class Chi0:
 
     def synchronize(self):
         self._check(_lib.chi0_synchronize(self.h))
+
+    def term_features(self, iq, chi_trunc, x, chi_full=None, t=None):
+        """Features (and targets) of a truncated chi0 held on the device; returns the scale c."""
+        sc = ctypes.c_double()
+        self._check(_lib.chi0_term_features(self.h, int(iq), _dev(chi_trunc),
+                                            _dev(chi_full) if chi_full is not None else None, _dev(x),
+                                            _dev(t) if t is not None else None, ctypes.byref(sc)))
+        return sc.value
+
+    def set_terminator(self, params, bf16=True):
+        self._check(_lib.chi0_set_terminator(self.h, _dev(params) if params is not None else None,
+                                             int(bool(bf16))))
 
     STAGES = ("wf_grid", "rho", "weights", "contract", "reduce", "dyson")
 

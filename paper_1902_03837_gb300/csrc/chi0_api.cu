@@ -576,6 +576,11 @@ chi0_status chi0_build_chi0(chi0_ctx* c, int iq, void* out, int out_on_device) {
       if (s != CHI0_OK) return s;
     }
   }
+  if (c->term_params && c->nt > 0) {
+    s = chi0::term_apply_ctx(c, iq, (double2*)c->d_chi.p);
+    if (s != CHI0_OK) return s;
+    c->launches += 3;
+  }
   c->chi_iq = iq;
   c->eps_iq = -1;
   if (out) {
@@ -757,7 +762,8 @@ void chi0_destroy(chi0_ctx* c) {
   DevBuf* bufs[] = {&c->d_gvec, &c->d_npw, &c->d_coef, &c->d_eps, &c->d_occ, &c->d_stage,
                     &c->d_gresp, &c->d_gperm, &c->d_kq, &c->d_g0, &c->d_tw1, &c->d_tw2, &c->d_U, &c->d_R,
                     &c->d_w, &c->d_part, &c->d_chi, &c->d_A, &c->d_colp, &c->d_rowp, &c->d_pinv,
-                    &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc};
+                    &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
+                    &c->d_termq, &c->d_termw, &c->d_termc};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)

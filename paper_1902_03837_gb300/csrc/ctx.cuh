@@ -46,6 +46,10 @@ struct chi0_ctx {
       d_pinv, d_err, d_vsqrt, d_omim, d_tc;
   int nchunks = 1, kchunk = 0;
   void* tc = nullptr;  // tensor-core path state (tc.cu)
+  // learned terminator (terminator.cu)
+  const float* term_params = nullptr;  // device parameters; NULL = off
+  int term_bf16 = 1;
+  DevBuf d_termx, d_termy, d_termq, d_termw, d_termc;
 
   // per-stage device time: CUDA event pairs on the context's stream, summed
   // over every launch of the stage since the last chi0_get_stats
@@ -74,4 +78,9 @@ void stage_end(chi0_ctx* c, int stage, int kernels);
 chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                           double2* chi);
 void tc_release(chi0_ctx* c);
+// learned terminator: network kernels and the correction of a built chi0
+int mlp_nparams();
+cudaError_t mlp_predict(const float* prm, const float* x, int64_t batch, int bf16, float* y,
+                        cudaStream_t st);
+chi0_status term_apply_ctx(chi0_ctx* c, int iq, double2* chi);
 }  // namespace chi0

@@ -376,9 +376,15 @@ __global__ void __launch_bounds__(256)
 k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, int ng, int mpad,
        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   __shared__ float tile[2 * kPI][kPT + 1];
+  __shared__ float ws[kPT];  // weights of the tile's transitions, converted once (FP64 is slow here)
   const int64_t kb = blockIdx.x;
   const int64_t t0 = kb * kPT;
   const int i0 = blockIdx.y * kPI;
+  if (threadIdx.x < kPT) {
+    const int64_t t = t0 + threadIdx.x;
+    ws[threadIdx.x] = (w && t < nt) ? (float)w[t] : 1.f;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
     const int tl = e / kPI, il = e % kPI;
     const int64_t t = t0 + tl;
@@ -386,11 +392,9 @@ k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, i
     float2 v = make_float2(0.f, 0.f);
     if (t < nt && i < ng) {
       v = R[t * ng + i];
-      if (w) {
-        const float s = (float)w[t];
-        v.x *= s;
-        v.y *= s;
-      }
+      const float s = ws[tl];
+      v.x *= s;
+      v.y *= s;
     }
     tile[2 * il][tl] = v.x;
     tile[2 * il + 1][tl] = v.y;

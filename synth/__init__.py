@@ -13,6 +13,8 @@ from .systems import (  # noqa: F401
     System,
     make_system,
     make_plane_wave_system,
+    truncate_bands,
+    cfg_learned,
     cfg_plain_fp64,
     cfg_precision,
     cfg_tiny,

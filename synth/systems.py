@@ -317,3 +317,24 @@ def make_plane_wave_system(spec: SystemSpec, e_fermi: float) -> System:
                   freqs=np.array(spec.freqs, dtype=np.complex128).reshape(-1),
                   eta=float(spec.eta), spin_factor=float(spec.spin_factor),
                   fft=tuple(int(v) for v in spec.fft), ng=int(spec.ng))
+
+
+def truncate_bands(system: System, nb: int) -> System:
+    """The same crystal described with only its first nb bands (coefficients,
+    energies and occupations of bands 0..nb-1)."""
+    spec = dataclasses.replace(system.spec, n_bands=nb)
+    return dataclasses.replace(system, spec=spec, coef=np.ascontiguousarray(system.coef[:, :nb]),
+                               eps=np.ascontiguousarray(system.eps[:, :nb]),
+                               occ=np.ascontiguousarray(system.occ[:, :nb]))
+
+
+def cfg_learned(seed: int = 4000, full_bands: int = 800, n_occ: int = 12, kgrid=(6, 6, 6),
+                kc: float = 4.4601, fft=(32, 32, 32), ng: int = 500, nw: int = 16) -> SystemSpec:
+    """Learned-terminator case: 6x6x6 k, 12 occupied bands, ~1500 PW, FFT 32^3,
+    N_G = 500, q = (1/6,0,0), 16 imaginary frequencies on [0, 100] eV; the
+    truncated chi0 uses the first bands of the same system.  Smaller variants
+    (for tests) override the keyword arguments."""
+    q = (1.0 / kgrid[0], 0.0, 0.0)
+    return SystemSpec(a=10.0, kgrid=tuple(kgrid), n_occ=n_occ, n_bands=full_bands, kc=kc,
+                      fft=tuple(fft), ng=ng, q_frac=(q,), freqs=tuple(gauss_legendre_freqs(nw, 0.0, 100.0)),
+                      eta=0.0, seed=seed, coef_dtype="c64")
