@@ -213,6 +213,38 @@ chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms, double* bytes, double* flo
 chi0_status chi0_invert_eps_noalloc(const void* chi0, const double* v_sqrt, int ng, int nw,
                                     void* out, void* cuda_stream);
 
+/* ---- Batched problems -------------------------------------------------------
+ * The paper spreads the response function over q points and transitions
+ * (Parallelism section, linear response) and notes that q points are uneven
+ * because the number of transitions varies.  A batch runs many independent
+ * problems -- n contexts, each at its own q index iqs[i] -- as one unit: all
+ * host set-up at creation, the oscillator strengths of every problem in one
+ * persistent launch over a device task table, the remaining kernels of the
+ * problems on `nstreams` helper streams, everything captured once into a CUDA
+ * graph that each chi0_batch_run replays.  The rho tile width is timed on the
+ * batch's own data at creation and remembered per geometry in the process.
+ *   eps_out: NULL, or n device pointers to [nw_i][ng_i][ng_i] complex128
+ *            receiving eps~^-1 of each problem (NULL entries skip the Dyson
+ *            step of that problem); chi0 of problem i stays in its context.
+ * All contexts must share one precision and be distinct; their wavefunctions
+ * and energies must be set.  While the batch exists, call no other entry
+ * point that computes on its contexts (they own the buffers the graph uses).
+ * Errors: CHI0_EINVAL, CHI0_ESTATE, CHI0_EUNSUPPORTED (mixed precisions, or a
+ * problem too large for one persistent launch), CHI0_ENOMEM, CHI0_ECUDA. */
+typedef struct chi0_batch chi0_batch;
+
+chi0_status chi0_batch_create(chi0_ctx* const* ctxs, const int* iqs, void* const* eps_out, int n,
+                              int nstreams, chi0_batch** out);
+
+/* Replay the batch on `stream` (asynchronous; the first call captures the
+ * graph).  Device-side errors are read with chi0_synchronize on a context. */
+chi0_status chi0_batch_run(chi0_batch* b, void* stream);
+
+/* m bands per block chosen for the persistent rho launch (1, 2 or 4). */
+int chi0_batch_rho_width(const chi0_batch* b);
+
+void chi0_batch_destroy(chi0_batch* b);
+
 /* ---- Learned band-sum terminator -------------------------------------------
  * The paper's X-terminator (Linear Response section, Eq. X_term_def; its
  * expressions in Appendix C) corrects a band-truncated chi0 by an extra term

@@ -29,6 +29,7 @@ EXPORTS = (
     "chi0_get_rho", "chi0_get_rho_rows", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator",
+    "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
 )
 
 
@@ -89,10 +90,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_mlp_predict.argtypes = [P, P, I64, I, P, P]
     lib.chi0_term_features.argtypes = [P, I, P, P, P, P, P]
     lib.chi0_set_terminator.argtypes = [P, P, I]
+    lib.chi0_batch_create.argtypes = [P, P, P, I, I, ctypes.POINTER(P)]
+    lib.chi0_batch_run.argtypes = [P, P]
+    lib.chi0_batch_rho_width.argtypes = [P]
+    lib.chi0_batch_destroy.argtypes = [P]
     for name in EXPORTS:
-        if name not in ("chi0_last_error", "chi0_destroy"):
+        if name not in ("chi0_last_error", "chi0_destroy", "chi0_batch_destroy"):
             getattr(lib, name).restype = I
     lib.chi0_mlp_workspace_floats.restype = I64
+    lib.chi0_batch_destroy.restype = None
     del D
     return lib
 
@@ -127,6 +133,45 @@ def invert_eps_noalloc(chi0, v_sqrt, out, stream=None):
     if st != 0:
         raise Chi0Error(st, "chi0_invert_eps_noalloc failed")
     return out
+
+
+class Batch:
+    """chi0_batch: many (context, q index) problems run as one captured graph."""
+
+    def __init__(self, ctxs, iqs, eps_out=None, nstreams=4):
+        n = len(ctxs)
+        self._ctxs = list(ctxs)          # keep the contexts alive
+        self._outs = list(eps_out) if eps_out is not None else None
+        hs = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
+        qs = (ctypes.c_int * n)(*[int(q) for q in iqs])
+        outs = None
+        if eps_out is not None:
+            outs = (ctypes.c_void_p * n)(*[(_dev(o) if o is not None else None) for o in eps_out])
+        h = ctypes.c_void_p()
+        st = _lib.chi0_batch_create(hs, qs, outs, n, int(nstreams), ctypes.byref(h))
+        if st != 0:
+            raise Chi0Error(st, "chi0_batch_create failed: " +
+                            "; ".join(_lib.chi0_last_error(c.h).decode(errors="replace") for c in ctxs))
+        self.h = h
+
+    def run(self, stream=None):
+        st = _lib.chi0_batch_run(self.h, stream)
+        if st != 0:
+            raise Chi0Error(st, "chi0_batch_run failed")
+
+    def rho_width(self):
+        return int(_lib.chi0_batch_rho_width(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.chi0_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- learned terminator network (device tensors: float32, contiguous)

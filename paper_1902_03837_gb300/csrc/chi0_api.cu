@@ -63,6 +63,7 @@ chi0_status ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) {
 
 namespace chi0 {
 void stage_begin(chi0_ctx* c, int stage) {
+  if (c->capturing) return;
   auto& st = c->stage[stage];
   if (st.used + 2 > st.ev.size()) {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -77,6 +78,11 @@ void stage_begin(chi0_ctx* c, int stage) {
 }
 void stage_end(chi0_ctx* c, int stage, int kernels) {
   auto& st = c->stage[stage];
+  if (c->capturing) {
+    st.launches += kernels;
+    c->launches += kernels;
+    return;
+  }
   if (st.used + 2 > st.ev.size()) return;  // begin failed to get events
   cudaEventRecord(st.ev[st.used + 1], c->st);
   st.used += 2;
@@ -188,6 +194,329 @@ chi0_status check_device_error(chi0_ctx* c) {
 }
 
 }  // namespace
+
+namespace chi0 {
+
+chi0_status plan_rho(chi0_ctx* c, int iq) {
+  if (!c) return CHI0_EINVAL;
+  if (iq < 0 || iq >= c->cfg.nq) return fail(c, CHI0_EINVAL, "iq %d out of range", iq);
+  for (int ik = 0; ik < c->nk; ++ik)
+    if (!c->wf_set[ik]) return fail(c, CHI0_ESTATE, "wavefunctions of k %d not set", ik);
+  if (!c->energies_set) return fail(c, CHI0_ESTATE, "energies not set");
+  chi0_status s;
+  // ---- q-point setup on the host
+  response_set(c, iq, c->h_gresp);
+  kpairs(c, iq, c->h_kq, c->h_g0);
+  const double tol = c->cfg.occ_drop_tol;
+  int mmax = -1, nmin = c->nb;
+  for (int ik = 0; ik < c->nk; ++ik)
+    for (int b = 0; b < c->nb; ++b) {
+      const double f = c->h_occ[(size_t)ik * c->nb + b];
+      if (f > tol) mmax = std::max(mmax, b);
+      if (f < 1.0 - tol) nmin = std::min(nmin, b);
+    }
+  c->Nm = mmax + 1;
+  c->n_lo = nmin;
+  c->Nn = c->nb - nmin;
+  c->nt = (int64_t)c->nk * c->Nn * c->Nm;
+  RhoGeom& g = c->geom;
+  g = RhoGeom{};
+  g.N1 = c->cfg.fft[0];
+  g.N2 = c->cfg.fft[1];
+  g.N3 = c->cfg.fft[2];
+  int L[3] = {0, 0, 0};
+  for (int ik = 0; ik < c->nk; ++ik)
+    for (int p = 0; p < c->h_npw[ik]; ++p)
+      for (int d = 0; d < 3; ++d)
+        L[d] = std::max(L[d], std::abs(c->h_gvec[((size_t)ik * c->npw_max + p) * 3 + d]));
+  g.Lx = L[0];
+  g.Ly = L[1];
+  g.Lz = L[2];
+  g.NX = 2 * L[0] + 1;
+  g.NY = 2 * L[1] + 1;
+  g.NZ = 2 * L[2] + 1;
+  g.nk = c->nk;
+  g.nb = c->nb;
+  g.npw_max = c->npw_max;
+  g.ng = c->cfg.ng;
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int i = 0; i < g.ng; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], c->h_gresp[3 * i + d]);
+      hi[d] = std::max(hi[d], c->h_gresp[3 * i + d]);
+    }
+  g.Mx_lo = lo[0];
+  g.My_lo = lo[1];
+  g.Mz_lo = lo[2];
+  g.HX = hi[0] - lo[0] + 1;
+  g.HY = hi[1] - lo[1] + 1;
+  g.HZ = hi[2] - lo[2] + 1;
+  g.n_lo = c->n_lo;
+  g.Nn = c->Nn;
+  g.Nm = c->Nm;
+  int g0max = 0;
+  for (int v : c->h_g0) g0max = std::max(g0max, std::abs(v));
+  g.g0max = g0max;
+  g.g0z_min = 1 << 30;
+  g.g0z_max = -(1 << 30);
+  for (int ik = 0; ik < c->nk; ++ik) {
+    g.g0z_min = std::min(g.g0z_min, c->h_g0[3 * ik + 2]);
+    g.g0z_max = std::max(g.g0z_max, c->h_g0[3 * ik + 2]);
+  }
+  // response indices in (Gy, Gz, Gx) order
+  c->h_gperm.resize(g.ng);
+  for (int i = 0; i < g.ng; ++i) c->h_gperm[i] = i;
+  std::stable_sort(c->h_gperm.begin(), c->h_gperm.end(), [&](int a, int b) {
+    const int32_t* A = &c->h_gresp[3 * a];
+    const int32_t* B = &c->h_gresp[3 * b];
+    if (A[1] != B[1]) return A[1] < B[1];
+    if (A[2] != B[2]) return A[2] < B[2];
+    return A[0] < B[0];
+  });
+  // the real-space product must not alias onto the response set
+  for (int d = 0; d < 3; ++d) {
+    const int n = c->cfg.fft[d];
+    const int hmax = std::max(std::abs(lo[d]), std::abs(hi[d])) + g0max;
+    if (n <= 2 * L[d] + hmax)
+      return fail(c, CHI0_EINVAL,
+                  "fft[%d] = %d aliases: need > 2*%d + %d for these spheres and response set", d,
+                  n, L[d], hmax);
+  }
+  c->rho_iq = c->chi_iq = c->eps_iq = -1;
+  c->plan_rho_iq = iq;
+  if (c->nt == 0) return CHI0_OK;
+  // ---- device buffers
+  const size_t cb = cplx_bytes(c);
+  const size_t ubytes = (size_t)c->nk * c->nb * g.N1 * g.NZ * g.N2 * cb;
+  if ((s = ensure(c, c->d_U, ubytes, "mixed-grid wavefunctions")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_R, (size_t)c->nt * g.ng * cb, "rho")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_gresp, (size_t)g.ng * 12, "G set")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_gperm, (size_t)g.ng * 4, "G order")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_kq, (size_t)c->nk * 4, "k pairs")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_g0, (size_t)c->nk * 12, "umklapp")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_tw1, (size_t)g.N1 * cb, "twiddles")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_tw2, (size_t)g.N2 * cb, "twiddles")) != CHI0_OK) return s;
+  CK(cudaMemcpyAsync(c->d_gresp.p, c->h_gresp.data(), (size_t)g.ng * 12, cudaMemcpyHostToDevice, c->st), "G set H2D");
+  CK(cudaMemcpyAsync(c->d_kq.p, c->h_kq.data(), (size_t)c->nk * 4, cudaMemcpyHostToDevice, c->st), "kq H2D");
+  CK(cudaMemcpyAsync(c->d_gperm.p, c->h_gperm.data(), (size_t)g.ng * 4, cudaMemcpyHostToDevice, c->st), "G order H2D");
+  CK(cudaMemcpyAsync(c->d_g0.p, c->h_g0.data(), (size_t)c->nk * 12, cudaMemcpyHostToDevice, c->st), "g0 H2D");
+  if (c->fp64) {
+    std::vector<double2> t1, t2;
+    twiddles(g.N1, t1);
+    twiddles(g.N2, t2);
+    CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  } else {
+    std::vector<double2> t1d, t2d;
+    twiddles(g.N1, t1d);
+    twiddles(g.N2, t2d);
+    std::vector<float2> t1(t1d.size()), t2(t2d.size());
+    for (size_t i = 0; i < t1d.size(); ++i) t1[i] = make_float2((float)t1d[i].x, (float)t1d[i].y);
+    for (size_t i = 0; i < t2d.size(); ++i) t2[i] = make_float2((float)t2d[i].x, (float)t2d[i].y);
+    CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  }
+  // mixed grid: coefficients in, U out; transforms along y (NX N2 NY per gz
+  // plane) and x (N1 N2 NX per gz plane)
+  {
+    auto& a1 = c->stage[CHI0_STAGE_WF_GRID];
+    a1.bytes = (double)c->nk * c->nb * ((double)c->npw_max * (cb + 12) + ubytes / ((double)c->nk * c->nb));
+    a1.flops = 8.0 * (double)c->nk * c->nb * g.NZ *
+               ((double)g.NX * g.N2 * g.NY + (double)g.N1 * g.N2 * g.NX);
+    // rho: every transition reads two N1 x NZ x N2 mixed grids and writes ng values;
+    // executed complex multiply-adds per transition and x plane: the z
+    // correlation (N2 HZ NZ), the pruned y transform (HY HZ N2), the x
+    // accumulation (ng)
+    auto& a2 = c->stage[CHI0_STAGE_RHO];
+    a2.bytes = (double)c->nt * g.ng * cb + (double)ubytes;
+    a2.flops = 8.0 * (double)c->nt * g.N1 *
+               ((double)g.N2 * g.HZ * g.NZ + (double)g.HY * g.HZ * g.N2 + (double)g.ng);
+  }
+  return CHI0_OK;
+}
+
+// kernels of compute_rho (wavefunctions to the mixed grid; rho unless the
+// caller runs rho for many problems in one batched launch)
+chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
+  const int iq = c->plan_rho_iq;
+  if (iq < 0) return fail(c, CHI0_ESTATE, "rho not planned");
+  if (c->nt > 0) {
+    const RhoGeom& g = c->geom;
+    cudaError_t e;
+    chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
+    if (c->fp64)
+      e = chi0::launch_wf_to_mixed<double>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
+                                           (const double2*)c->d_coef.p, (const double2*)c->d_tw1.p,
+                                           (const double2*)c->d_tw2.p, (double2*)c->d_U.p, c->st);
+    else
+      e = chi0::launch_wf_to_mixed<float>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
+                                          (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
+                                          (const float2*)c->d_tw2.p, (float2*)c->d_U.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
+    if (with_pairs) {
+      chi0::stage_begin(c, CHI0_STAGE_RHO);
+      if (c->fp64)
+        e = chi0::launch_rho_pairs<double, double2>(
+            g, (const double2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+            (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const double2*)c->d_tw1.p,
+            (const double2*)c->d_tw2.p, (double2*)c->d_R.p, c->st);
+      else
+        e = chi0::launch_rho_pairs<float, float2>(
+            g, (const float2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+            (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p,
+            (const float2*)c->d_tw2.p, (float2*)c->d_R.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
+      chi0::stage_end(c, CHI0_STAGE_RHO, 1);
+    }
+  }
+  c->rho_iq = iq;
+  c->chi_iq = c->eps_iq = -1;
+  return CHI0_OK;
+}
+
+chi0_status plan_chi0(chi0_ctx* c, int iq) {
+  if (iq != c->plan_rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  for (int iw = 0; iw < nw; ++iw)
+    if (c->om[2 * iw] != 0.0)
+      return fail(c, CHI0_EUNSUPPORTED, "frequency %d has a real part: non-Hermitian chi0 not supported", iw);
+  chi0_status s;
+  const size_t n2 = (size_t)ng * ng;
+  if ((s = ensure(c, c->d_chi, n2 * nw * 16, "chi0")) != CHI0_OK) return s;
+  if (!c->d_err.p) {
+    if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
+    CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
+  }
+  c->plan_chi_iq = -1;
+  if (c->nt > 0) {
+    if ((s = ensure(c, c->d_w, (size_t)c->nt * nw * 8, "weights")) != CHI0_OK) return s;
+    if ((s = ensure(c, c->d_omim, (size_t)nw * 8, "frequencies")) != CHI0_OK) return s;
+    std::vector<double> omim(nw);
+    for (int iw = 0; iw < nw; ++iw) omim[iw] = c->om[2 * iw + 1];
+    CK(cudaMemcpyAsync(c->d_omim.p, omim.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    if (c->fp64) {
+      // split the transitions into chunks so that the grid fills the GPU
+      const int nT = (ng + 31) / 32;
+      const int64_t tiles = (int64_t)nT * (nT + 1) / 2 * nw;
+      int64_t want = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
+      const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(8ull << 30) / (int64_t)(n2 * nw * 16));
+      want = std::min<int64_t>({want, mem_cap, (c->nt + 63) / 64});
+      c->nchunks = (int)std::max<int64_t>(1, want);
+      c->kchunk = (int)((c->nt + c->nchunks - 1) / c->nchunks);
+      if ((s = ensure(c, c->d_part, n2 * nw * c->nchunks * 16, "chi0 partials")) != CHI0_OK) return s;
+    } else {
+      if ((s = chi0::tc_plan(c, c->nt, ng, nw)) != CHI0_OK) return s;
+    }
+    if (c->term_params && (s = chi0::term_plan(c, iq)) != CHI0_OK) return s;
+  }
+  c->plan_chi_iq = iq;
+  return CHI0_OK;
+}
+
+// kernels of build_chi0 (weights, contraction, reduction, terminator)
+chi0_status launch_chi0(chi0_ctx* c) {
+  const int iq = c->plan_chi_iq;
+  if (iq < 0) return fail(c, CHI0_ESTATE, "chi0 not planned");
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  const size_t n2 = (size_t)ng * ng;
+  chi0_status s;
+  if (c->nt == 0) {
+    CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw * 16, c->st), "zero chi0");
+  } else {
+    const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
+    chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
+    cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
+                                         (const double*)c->d_eps.p, (const double*)c->d_occ.p,
+                                         (const double*)c->d_omim.p, nullptr, nw, c->cfg.eta, pref,
+                                         c->cfg.occ_drop_tol, (double*)c->d_w.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
+    chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+    c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
+    c->stage[CHI0_STAGE_WEIGHTS].flops = 6.0 * (double)c->nt * nw;
+    // chi0 algorithmic flops (Hermitian half): 4 ng (ng + 1) nt per frequency
+    c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)c->nt * nw;
+    c->stage[CHI0_STAGE_CONTRACT].bytes = (double)c->nt * ng * cplx_bytes(c) + (double)c->nt * nw * 8;
+    c->stage[CHI0_STAGE_REDUCE].bytes = (double)n2 * nw * 16;
+    c->stage[CHI0_STAGE_REDUCE].flops = 0;
+    if (c->fp64) {
+      chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
+      e = chi0::launch_chi0_fp64_partials((const double2*)c->d_R.p, (const double*)c->d_w.p, c->nt, ng,
+                                          nw, c->kchunk, c->nchunks, (double2*)c->d_part.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "chi0 fp64 launch");
+      chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
+      chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+      e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw,
+                                   (double2*)c->d_chi.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch");
+      chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+      c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
+    } else {
+      s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p);
+      if (s != CHI0_OK) return s;
+    }
+    if (c->term_params) {
+      s = chi0::term_launch(c, (double2*)c->d_chi.p);
+      if (s != CHI0_OK) return s;
+    }
+  }
+  c->chi_iq = iq;
+  c->eps_iq = -1;
+  return CHI0_OK;
+}
+
+chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
+  if (iq != c->plan_chi_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_build_chi0(%d) must come first", iq);
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  chi0_status s;
+  if ((s = ensure(c, c->d_vsqrt, (size_t)ng * 8, "coulomb")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_colp, (size_t)nw * ng * 32 * 16, "panels")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_rowp, (size_t)nw * ng * 32 * 16, "panels")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_pinv, (size_t)nw * 32 * 32 * 16, "pivot blocks")) != CHI0_OK) return s;
+  std::vector<double> v(ng);
+  int64_t qi[3];
+  q_integers(c, iq, qi);
+  for (int i = 0; i < ng; ++i) {
+    double q2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double comp = (double)qi[d] / c->cfg.kgrid[d] + c->h_gresp[3 * i + d];
+      q2 += comp * comp;
+    }
+    const double qg = (2.0 * M_PI / c->a) * std::sqrt(q2);
+    if (qg == 0.0) return fail(c, CHI0_EINVAL, "|q+G| = 0: bare Coulomb interaction diverges");
+    v[i] = std::sqrt(4.0 * M_PI) / qg;
+  }
+  CK(cudaMemcpyAsync(c->d_vsqrt.p, v.data(), ng * 8, cudaMemcpyHostToDevice, c->st), "v H2D");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  c->plan_eps_out = A;
+  c->plan_eps_iq = iq;
+  return CHI0_OK;
+}
+
+// kernels of invert_eps (eps~ and the Gauss-Jordan inverse into the planned output)
+chi0_status launch_eps(chi0_ctx* c) {
+  const int iq = c->plan_eps_iq;
+  if (iq < 0) return fail(c, CHI0_ESTATE, "Dyson step not planned");
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  const size_t n2 = (size_t)ng * ng;
+  chi0::stage_begin(c, CHI0_STAGE_DYSON);
+  cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p, (const double*)c->d_vsqrt.p, ng, nw,
+                                     c->plan_eps_out, (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
+                                     (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
+  chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * ((ng + 31) / 32));
+  // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency (about
+  // half of them executed, the Hermitian lower tiles)
+  c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
+  c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
+  c->eps_iq = iq;
+  return CHI0_OK;
+}
+
+}  // namespace chi0
 
 extern "C" {
 
@@ -344,247 +673,20 @@ chi0_status chi0_set_energies(chi0_ctx* c, const double* eps, const double* occ)
 
 chi0_status chi0_compute_rho(chi0_ctx* c, int iq) {
   if (!c) return CHI0_EINVAL;
-  if (iq < 0 || iq >= c->cfg.nq) return fail(c, CHI0_EINVAL, "iq %d out of range", iq);
-  for (int ik = 0; ik < c->nk; ++ik)
-    if (!c->wf_set[ik]) return fail(c, CHI0_ESTATE, "wavefunctions of k %d not set", ik);
-  if (!c->energies_set) return fail(c, CHI0_ESTATE, "energies not set");
   chi0_status s;
-  // ---- q-point setup on the host
-  response_set(c, iq, c->h_gresp);
-  kpairs(c, iq, c->h_kq, c->h_g0);
-  const double tol = c->cfg.occ_drop_tol;
-  int mmax = -1, nmin = c->nb;
-  for (int ik = 0; ik < c->nk; ++ik)
-    for (int b = 0; b < c->nb; ++b) {
-      const double f = c->h_occ[(size_t)ik * c->nb + b];
-      if (f > tol) mmax = std::max(mmax, b);
-      if (f < 1.0 - tol) nmin = std::min(nmin, b);
-    }
-  c->Nm = mmax + 1;
-  c->n_lo = nmin;
-  c->Nn = c->nb - nmin;
-  c->nt = (int64_t)c->nk * c->Nn * c->Nm;
-  RhoGeom& g = c->geom;
-  g = RhoGeom{};
-  g.N1 = c->cfg.fft[0];
-  g.N2 = c->cfg.fft[1];
-  g.N3 = c->cfg.fft[2];
-  int L[3] = {0, 0, 0};
-  for (int ik = 0; ik < c->nk; ++ik)
-    for (int p = 0; p < c->h_npw[ik]; ++p)
-      for (int d = 0; d < 3; ++d)
-        L[d] = std::max(L[d], std::abs(c->h_gvec[((size_t)ik * c->npw_max + p) * 3 + d]));
-  g.Lx = L[0];
-  g.Ly = L[1];
-  g.Lz = L[2];
-  g.NX = 2 * L[0] + 1;
-  g.NY = 2 * L[1] + 1;
-  g.NZ = 2 * L[2] + 1;
-  g.nk = c->nk;
-  g.nb = c->nb;
-  g.npw_max = c->npw_max;
-  g.ng = c->cfg.ng;
-  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
-  for (int i = 0; i < g.ng; ++i)
-    for (int d = 0; d < 3; ++d) {
-      lo[d] = std::min(lo[d], c->h_gresp[3 * i + d]);
-      hi[d] = std::max(hi[d], c->h_gresp[3 * i + d]);
-    }
-  g.Mx_lo = lo[0];
-  g.My_lo = lo[1];
-  g.Mz_lo = lo[2];
-  g.HX = hi[0] - lo[0] + 1;
-  g.HY = hi[1] - lo[1] + 1;
-  g.HZ = hi[2] - lo[2] + 1;
-  g.n_lo = c->n_lo;
-  g.Nn = c->Nn;
-  g.Nm = c->Nm;
-  int g0max = 0;
-  for (int v : c->h_g0) g0max = std::max(g0max, std::abs(v));
-  g.g0max = g0max;
-  g.g0z_min = 1 << 30;
-  g.g0z_max = -(1 << 30);
-  for (int ik = 0; ik < c->nk; ++ik) {
-    g.g0z_min = std::min(g.g0z_min, c->h_g0[3 * ik + 2]);
-    g.g0z_max = std::max(g.g0z_max, c->h_g0[3 * ik + 2]);
-  }
-  // response indices in (Gy, Gz, Gx) order
-  c->h_gperm.resize(g.ng);
-  for (int i = 0; i < g.ng; ++i) c->h_gperm[i] = i;
-  std::stable_sort(c->h_gperm.begin(), c->h_gperm.end(), [&](int a, int b) {
-    const int32_t* A = &c->h_gresp[3 * a];
-    const int32_t* B = &c->h_gresp[3 * b];
-    if (A[1] != B[1]) return A[1] < B[1];
-    if (A[2] != B[2]) return A[2] < B[2];
-    return A[0] < B[0];
-  });
-  // the real-space product must not alias onto the response set
-  for (int d = 0; d < 3; ++d) {
-    const int n = c->cfg.fft[d];
-    const int hmax = std::max(std::abs(lo[d]), std::abs(hi[d])) + g0max;
-    if (n <= 2 * L[d] + hmax)
-      return fail(c, CHI0_EINVAL,
-                  "fft[%d] = %d aliases: need > 2*%d + %d for these spheres and response set", d,
-                  n, L[d], hmax);
-  }
-  if (c->nt == 0) {
-    c->rho_iq = iq;
-    c->chi_iq = c->eps_iq = -1;
-    return CHI0_OK;
-  }
-  // ---- device buffers
-  const size_t cb = cplx_bytes(c);
-  const size_t ubytes = (size_t)c->nk * c->nb * g.N1 * g.NZ * g.N2 * cb;
-  if ((s = ensure(c, c->d_U, ubytes, "mixed-grid wavefunctions")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_R, (size_t)c->nt * g.ng * cb, "rho")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_gresp, (size_t)g.ng * 12, "G set")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_gperm, (size_t)g.ng * 4, "G order")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_kq, (size_t)c->nk * 4, "k pairs")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_g0, (size_t)c->nk * 12, "umklapp")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_tw1, (size_t)g.N1 * cb, "twiddles")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_tw2, (size_t)g.N2 * cb, "twiddles")) != CHI0_OK) return s;
-  CK(cudaMemcpyAsync(c->d_gresp.p, c->h_gresp.data(), (size_t)g.ng * 12, cudaMemcpyHostToDevice, c->st), "G set H2D");
-  CK(cudaMemcpyAsync(c->d_kq.p, c->h_kq.data(), (size_t)c->nk * 4, cudaMemcpyHostToDevice, c->st), "kq H2D");
-  CK(cudaMemcpyAsync(c->d_gperm.p, c->h_gperm.data(), (size_t)g.ng * 4, cudaMemcpyHostToDevice, c->st), "G order H2D");
-  CK(cudaMemcpyAsync(c->d_g0.p, c->h_g0.data(), (size_t)c->nk * 12, cudaMemcpyHostToDevice, c->st), "g0 H2D");
-  cudaError_t e;
-  if (c->fp64) {
-    std::vector<double2> t1, t2;
-    twiddles(g.N1, t1);
-    twiddles(g.N2, t2);
-    CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
-    CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 16, cudaMemcpyHostToDevice, c->st), "tw H2D");
-    CK(cudaStreamSynchronize(c->st), "synchronize");
-    chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
-    e = chi0::launch_wf_to_mixed<double>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
-                                         (const double2*)c->d_coef.p, (const double2*)c->d_tw1.p,
-                                         (const double2*)c->d_tw2.p, (double2*)c->d_U.p, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
-    chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
-    chi0::stage_begin(c, CHI0_STAGE_RHO);
-    e = chi0::launch_rho_pairs<double, double2>(
-        g, (const double2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
-        (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const double2*)c->d_tw1.p, (const double2*)c->d_tw2.p,
-        (double2*)c->d_R.p, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
-  } else {
-    std::vector<double2> t1d, t2d;
-    twiddles(g.N1, t1d);
-    twiddles(g.N2, t2d);
-    std::vector<float2> t1(t1d.size()), t2(t2d.size());
-    for (size_t i = 0; i < t1d.size(); ++i) t1[i] = make_float2((float)t1d[i].x, (float)t1d[i].y);
-    for (size_t i = 0; i < t2d.size(); ++i) t2[i] = make_float2((float)t2d[i].x, (float)t2d[i].y);
-    CK(cudaMemcpyAsync(c->d_tw1.p, t1.data(), t1.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
-    CK(cudaMemcpyAsync(c->d_tw2.p, t2.data(), t2.size() * 8, cudaMemcpyHostToDevice, c->st), "tw H2D");
-    CK(cudaStreamSynchronize(c->st), "synchronize");
-    chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
-    e = chi0::launch_wf_to_mixed<float>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
-                                        (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
-                                        (const float2*)c->d_tw2.p, (float2*)c->d_U.p, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
-    chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
-    chi0::stage_begin(c, CHI0_STAGE_RHO);
-    e = chi0::launch_rho_pairs<float, float2>(
-        g, (const float2*)c->d_U.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
-        (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p, (const float2*)c->d_tw2.p,
-        (float2*)c->d_R.p, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
-  }
-  chi0::stage_end(c, CHI0_STAGE_RHO, 1);
-  // mixed grid: coefficients in, U out; transforms along y (NX N2 NY per gz
-  // plane) and x (N1 N2 NX per gz plane)
-  {
-    auto& a1 = c->stage[CHI0_STAGE_WF_GRID];
-    a1.bytes = (double)c->nk * c->nb * ((double)c->npw_max * (cb + 12) + ubytes / ((double)c->nk * c->nb));
-    a1.flops = 8.0 * (double)c->nk * c->nb * g.NZ *
-               ((double)g.NX * g.N2 * g.NY + (double)g.N1 * g.N2 * g.NX);
-    // rho: every transition reads two N1 x NZ x N2 mixed grids and writes ng values;
-    // executed complex multiply-adds per transition and x plane: the z
-    // correlation (N2 HZ NZ), the pruned y transform (HY HZ N2), the x
-    // accumulation (ng)
-    auto& a2 = c->stage[CHI0_STAGE_RHO];
-    a2.bytes = (double)c->nt * g.ng * cb + (double)ubytes;
-    a2.flops = 8.0 * (double)c->nt * g.N1 *
-               ((double)g.N2 * g.HZ * g.NZ + (double)g.HY * g.HZ * g.N2 + (double)g.ng);
-  }
-  c->rho_iq = iq;
-  c->chi_iq = c->eps_iq = -1;
-  return CHI0_OK;
+  if ((s = chi0::plan_rho(c, iq)) != CHI0_OK) return s;
+  return chi0::launch_rho(c, true);
 }
 
 chi0_status chi0_build_chi0(chi0_ctx* c, int iq, void* out, int out_on_device) {
   if (!c) return CHI0_EINVAL;
   if (iq != c->rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
-  const int nw = c->cfg.nw, ng = c->cfg.ng;
-  for (int iw = 0; iw < nw; ++iw)
-    if (c->om[2 * iw] != 0.0)
-      return fail(c, CHI0_EUNSUPPORTED, "frequency %d has a real part: non-Hermitian chi0 not supported", iw);
   chi0_status s;
-  const size_t n2 = (size_t)ng * ng;
-  if ((s = ensure(c, c->d_chi, n2 * nw * 16, "chi0")) != CHI0_OK) return s;
-  if (!c->d_err.p) {
-    if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
-    CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
-  }
-  if (c->nt == 0) {
-    CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw * 16, c->st), "zero chi0");
-  } else {
-    if ((s = ensure(c, c->d_w, (size_t)c->nt * nw * 8, "weights")) != CHI0_OK) return s;
-    if ((s = ensure(c, c->d_omim, (size_t)nw * 8, "frequencies")) != CHI0_OK) return s;
-    std::vector<double> omim(nw);
-    for (int iw = 0; iw < nw; ++iw) omim[iw] = c->om[2 * iw + 1];
-    CK(cudaMemcpyAsync(c->d_omim.p, omim.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
-    CK(cudaStreamSynchronize(c->st), "synchronize");
-    const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
-    chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
-    cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
-                                         (const double*)c->d_eps.p, (const double*)c->d_occ.p,
-                                         (const double*)c->d_omim.p, nullptr, nw, c->cfg.eta, pref,
-                                         c->cfg.occ_drop_tol, (double*)c->d_w.p, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
-    chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
-    c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
-    c->stage[CHI0_STAGE_WEIGHTS].flops = 6.0 * (double)c->nt * nw;
-    // chi0 algorithmic flops (Hermitian half): 4 ng (ng + 1) nt per frequency
-    c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)c->nt * nw;
-    c->stage[CHI0_STAGE_CONTRACT].bytes = (double)c->nt * ng * cplx_bytes(c) + (double)c->nt * nw * 8;
-    c->stage[CHI0_STAGE_REDUCE].bytes = (double)n2 * nw * 16;
-    c->stage[CHI0_STAGE_REDUCE].flops = 0;
-    if (c->fp64) {
-      // split the transitions into chunks so that the grid fills the GPU
-      const int nT = (ng + 31) / 32;
-      const int64_t tiles = (int64_t)nT * (nT + 1) / 2 * nw;
-      int64_t want = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
-      const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(8ull << 30) / (int64_t)(n2 * nw * 16));
-      want = std::min<int64_t>({want, mem_cap, (c->nt + 63) / 64});
-      c->nchunks = (int)std::max<int64_t>(1, want);
-      c->kchunk = (int)((c->nt + c->nchunks - 1) / c->nchunks);
-      if ((s = ensure(c, c->d_part, n2 * nw * c->nchunks * 16, "chi0 partials")) != CHI0_OK) return s;
-      chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
-      e = chi0::launch_chi0_fp64_partials((const double2*)c->d_R.p, (const double*)c->d_w.p, c->nt, ng,
-                                          nw, c->kchunk, c->nchunks, (double2*)c->d_part.p, c->st);
-      if (e != cudaSuccess) return cuda_fail(c, e, "chi0 fp64 launch");
-      chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
-      chi0::stage_begin(c, CHI0_STAGE_REDUCE);
-      e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw,
-                                   (double2*)c->d_chi.p, c->st);
-      if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch");
-      chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
-      c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
-    } else {
-      s = chi0::tc_build_chi0(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p);
-      if (s != CHI0_OK) return s;
-    }
-  }
-  if (c->term_params && c->nt > 0) {
-    s = chi0::term_apply_ctx(c, iq, (double2*)c->d_chi.p);
-    if (s != CHI0_OK) return s;
-    c->launches += 3;
-  }
-  c->chi_iq = iq;
-  c->eps_iq = -1;
+  if ((s = chi0::plan_chi0(c, iq)) != CHI0_OK) return s;
+  if ((s = chi0::launch_chi0(c)) != CHI0_OK) return s;
   if (out) {
-    CK(cudaMemcpyAsync(out, c->d_chi.p, n2 * nw * 16,
+    const size_t bytes = (size_t)c->cfg.ng * c->cfg.ng * c->cfg.nw * 16;
+    CK(cudaMemcpyAsync(out, c->d_chi.p, bytes,
                        out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st),
        "chi0 copy out");
     if (!out_on_device) {
@@ -599,48 +701,19 @@ chi0_status chi0_invert_eps(chi0_ctx* c, int iq, void* out, int out_on_device) {
   if (!c) return CHI0_EINVAL;
   if (iq != c->chi_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_build_chi0(%d) must come first", iq);
   if (!out) return fail(c, CHI0_EINVAL, "NULL output");
-  const int nw = c->cfg.nw, ng = c->cfg.ng;
-  const size_t n2 = (size_t)ng * ng;
+  const size_t bytes = (size_t)c->cfg.ng * c->cfg.ng * c->cfg.nw * 16;
   chi0_status s;
-  if ((s = ensure(c, c->d_vsqrt, (size_t)ng * 8, "coulomb")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_colp, (size_t)nw * ng * 32 * 16, "panels")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_rowp, (size_t)nw * ng * 32 * 16, "panels")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_pinv, (size_t)nw * 32 * 32 * 16, "pivot blocks")) != CHI0_OK) return s;
   double2* A;
   if (out_on_device) {
     A = (double2*)out;
   } else {
-    if ((s = ensure(c, c->d_A, n2 * nw * 16, "eps")) != CHI0_OK) return s;
+    if ((s = ensure(c, c->d_A, bytes, "eps")) != CHI0_OK) return s;
     A = (double2*)c->d_A.p;
   }
-  std::vector<double> v(ng);
-  int64_t qi[3];
-  q_integers(c, iq, qi);
-  for (int i = 0; i < ng; ++i) {
-    double q2 = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      const double comp = (double)qi[d] / c->cfg.kgrid[d] + c->h_gresp[3 * i + d];
-      q2 += comp * comp;
-    }
-    const double qg = (2.0 * M_PI / c->a) * std::sqrt(q2);
-    if (qg == 0.0) return fail(c, CHI0_EINVAL, "|q+G| = 0: bare Coulomb interaction diverges");
-    v[i] = std::sqrt(4.0 * M_PI) / qg;
-  }
-  CK(cudaMemcpyAsync(c->d_vsqrt.p, v.data(), ng * 8, cudaMemcpyHostToDevice, c->st), "v H2D");
-  CK(cudaStreamSynchronize(c->st), "synchronize");
-  chi0::stage_begin(c, CHI0_STAGE_DYSON);
-  cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p, (const double*)c->d_vsqrt.p, ng, nw, A,
-                                     (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
-                                     (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
-  if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
-  chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * ((ng + 31) / 32));
-  // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency (about
-  // half of them executed, the Hermitian lower tiles)
-  c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
-  c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
-  c->eps_iq = iq;
+  if ((s = chi0::plan_eps(c, iq, A)) != CHI0_OK) return s;
+  if ((s = chi0::launch_eps(c)) != CHI0_OK) return s;
   if (!out_on_device) {
-    CK(cudaMemcpyAsync(out, A, n2 * nw * 16, cudaMemcpyDeviceToHost, c->st), "eps copy out");
+    CK(cudaMemcpyAsync(out, A, bytes, cudaMemcpyDeviceToHost, c->st), "eps copy out");
     CK(cudaStreamSynchronize(c->st), "synchronize");
     return check_device_error(c);
   }

@@ -35,7 +35,10 @@ struct chi0_ctx {
   DevBuf d_gvec, d_npw, d_coef, d_eps, d_occ, d_stage;
 
   // q-point state
-  int rho_iq = -1, chi_iq = -1, eps_iq = -1;
+  int rho_iq = -1, chi_iq = -1, eps_iq = -1;      // completed (launched) steps
+  int plan_rho_iq = -1, plan_chi_iq = -1, plan_eps_iq = -1;  // planned steps
+  double2* plan_eps_out = nullptr;
+  bool capturing = false;  // inside a CUDA graph capture: no event timers
   std::vector<int32_t> h_gresp;  // [ng][3] of rho_iq
   std::vector<int32_t> h_kq, h_g0;
   std::vector<int> h_gperm;       // response indices in (Gy, Gz, Gx) order
@@ -75,12 +78,22 @@ void stage_begin(chi0_ctx* c, int stage);
 void stage_end(chi0_ctx* c, int stage, int kernels);
 // split-precision tensor-core contraction (mixed mode): chi[iw][i][j] from
 // R (complex64 [nt][ng]) and real weights w[iw][t]
-chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
-                          double2* chi);
+chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw);
+chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
+                      double2* chi);
 void tc_release(chi0_ctx* c);
 // learned terminator: network kernels and the correction of a built chi0
 int mlp_nparams();
 cudaError_t mlp_predict(const float* prm, const float* x, int64_t batch, int bf16, float* y,
                         cudaStream_t st);
-chi0_status term_apply_ctx(chi0_ctx* c, int iq, double2* chi);
+chi0_status term_plan(chi0_ctx* c, int iq);
+chi0_status term_launch(chi0_ctx* c, double2* chi);
+// plan (host set-up, allocation, uploads; may synchronise) and launch
+// (kernels only, capturable) halves of compute_rho / build_chi0 / invert_eps
+chi0_status plan_rho(chi0_ctx* c, int iq);
+chi0_status launch_rho(chi0_ctx* c, bool with_pairs);
+chi0_status plan_chi0(chi0_ctx* c, int iq);
+chi0_status launch_chi0(chi0_ctx* c);
+chi0_status plan_eps(chi0_ctx* c, int iq, double2* A);
+chi0_status launch_eps(chi0_ctx* c);
 }  // namespace chi0

@@ -32,6 +32,29 @@ struct RhoGeom {
   int g0z_min, g0z_max;    // range of G0_z over the k-pairs
 };
 
+// Zero padding of the n plane in the rho kernel's shared memory.
+struct RhoSmem {
+  int padz;      // zero rows below the n plane
+  int unp_rows;  // rows of the padded n plane (zero outside [padz, padz + NZ))
+};
+
+// One independent rho problem (a system at one q point) for the rho kernels.
+template <typename T, typename TOUT>
+struct RhoTask {
+  RhoGeom g;
+  RhoSmem sm;
+  const typename C2<T>::t* U;
+  const int32_t* kq;
+  const int32_t* g0;
+  const int32_t* gresp;
+  const int32_t* gperm;
+  const typename C2<T>::t* tw1;
+  const typename C2<T>::t* tw2;
+  TOUT* R;
+  int jm;          // m bands per block (<= the kernel's JM)
+  int64_t block0;  // first global block of this task in a batched launch
+};
+
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 
 // a1: sphere -> mixed grid U[k][band][x][gz][y] for every k and band.
@@ -49,6 +72,20 @@ cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const
                              const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
                              const typename C2<T>::t* tw1, const typename C2<T>::t* tw2,
                              TOUT* R, cudaStream_t s);
+
+// Fill a task for the rho kernels with at most jm_max m bands per block;
+// *smem = its shared memory with a JM = jm_max kernel, *nblocks its blocks.
+template <typename T, typename TOUT>
+cudaError_t rho_task_make(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
+                          const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
+                          const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
+                          int jm_max, RhoTask<T, TOUT>* tk, size_t* smem, int64_t* nblocks);
+
+// Persistent rho over many tasks in one launch (tasks_dev: device array with
+// block0 prefix offsets; total: all blocks; counter: device scratch).
+template <typename T, typename TOUT>
+cudaError_t launch_rho_batch(const RhoTask<T, TOUT>* tasks_dev, int ntasks, int64_t total, int jm,
+                             size_t smem, unsigned long long* counter, int nsm, cudaStream_t s);
 
 // a3: real transition weights w[iw][t] (FP64).
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,

@@ -149,10 +149,6 @@ constexpr int kHZT = 3;       // hz outputs per stage-Z work item
 constexpr int kHYT = 4;       // hy outputs per stage-Y work item
 constexpr int kHZY = 2;       // hz columns per stage-Y work item
 
-struct RhoSmem {
-  int padz;      // zero rows below the n plane
-  int unp_rows;  // rows of the padded n plane (zero outside [padz, padz + NZ))
-};
 
 template <typename T2, typename TOUT>
 __device__ __forceinline__ void store_out(TOUT* p, const T2 v, double scale);
@@ -165,24 +161,32 @@ __device__ __forceinline__ void store_out<float2, float2>(float2* p, const float
   *p = make_float2((float)(v.x * s), (float)(v.y * s));
 }
 
+// One block of transitions (one n at k, up to JM consecutive m at k - q) of
+// one task; blk is the block index within the task.
 template <typename T, int JM, typename TOUT>
-__global__ void __launch_bounds__(kRhoThreads)
-k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
-            const int32_t* __restrict__ kq, const int32_t* __restrict__ g0,
-            const int32_t* __restrict__ gresp, const int32_t* __restrict__ gperm,
-            const typename C2<T>::t* __restrict__ tw1,
-            const typename C2<T>::t* __restrict__ tw2, TOUT* __restrict__ R) {
+__device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t blk,
+                                          unsigned char* smem_raw) {
   using T2 = typename C2<T>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RhoGeom& g = tk.g;
+  const RhoSmem& sm = tk.sm;
+  const T2* __restrict__ U = tk.U;
+  const int32_t* __restrict__ kq = tk.kq;
+  const int32_t* __restrict__ g0 = tk.g0;
+  const int32_t* __restrict__ gresp = tk.gresp;
+  const int32_t* __restrict__ gperm = tk.gperm;
+  const T2* __restrict__ tw1 = tk.tw1;
+  const T2* __restrict__ tw2 = tk.tw2;
+  TOUT* __restrict__ R = tk.R;
+  const int jm = tk.jm;
   const int tid = threadIdx.x;
   // block order: m chunk fastest, then n, then the k-pair, so that the blocks
   // resident at one time share the mixed grids of one k-pair in L2
-  const int nmc = (g.Nm + JM - 1) / JM;
-  const int mc = blockIdx.x % nmc;
-  const int nrel = (blockIdx.x / nmc) % g.Nn;
-  const int ik = blockIdx.x / (nmc * g.Nn);
-  const int m0 = mc * JM;
-  const int cm = min(JM, g.Nm - m0);
+  const int nmc = (g.Nm + jm - 1) / jm;
+  const int mc = (int)(blk % nmc);
+  const int nrel = (int)((blk / nmc) % g.Nn);
+  const int ik = (int)(blk / ((int64_t)nmc * g.Nn));
+  const int m0 = mc * jm;
+  const int cm = min(jm, g.Nm - m0);
   const int ikp = kq[ik];
   const int G0x = g0[3 * ik], G0y = g0[3 * ik + 1], G0z = g0[3 * ik + 2];
   const int NZ = g.NZ, N2 = g.N2, HZ = g.HZ, HY = g.HY;
@@ -355,6 +359,42 @@ k_rho_pairs(RhoGeom g, RhoSmem sm, const typename C2<T>::t* __restrict__ U,
   }
 }
 
+template <typename T, int JM, typename TOUT>
+__global__ void __launch_bounds__(kRhoThreads) k_rho_pairs(const RhoTask<T, TOUT> tk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rho_block<T, JM, TOUT>(tk, blockIdx.x, smem_raw);
+}
+
+// Persistent form: every block takes the next global block index from a
+// device counter until all tasks' blocks are done.  Tasks are independent
+// problems (systems / q points) with their own geometry; task i owns global
+// blocks [block0_i, block0_{i+1}).
+template <typename T, int JM, typename TOUT>
+__global__ void __launch_bounds__(kRhoThreads)
+k_rho_batch(const RhoTask<T, TOUT>* __restrict__ tasks, int ntasks, int64_t total,
+            unsigned long long* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RhoTask<T, TOUT> stk;
+  __shared__ long long snext;
+  for (;;) {
+    if (threadIdx.x == 0) snext = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long gb = snext;
+    if (gb >= total) break;
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = ntasks - 1;  // last task with block0 <= gb
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (tasks[mid].block0 <= gb) lo = mid; else hi = mid - 1;
+      }
+      stk = tasks[lo];
+    }
+    __syncthreads();
+    rho_block<T, JM, TOUT>(stk, gb - stk.block0, smem_raw);
+    __syncthreads();
+  }
+}
+
 template <typename T>
 size_t rho_smem_bytes(const RhoGeom& g, const RhoSmem& sm, int jm) {
   using T2 = typename C2<T>::t;
@@ -381,28 +421,21 @@ cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int3
 }
 
 template <typename T, int JM, typename TOUT>
-static cudaError_t launch_rho_jm(const RhoGeom& g, const RhoSmem& sm, size_t smem,
-                                 const typename C2<T>::t* U, const int32_t* kq, const int32_t* g0,
-                                 const int32_t* gresp, const int32_t* gperm,
-                                 const typename C2<T>::t* tw1,
-                                 const typename C2<T>::t* tw2, TOUT* R, cudaStream_t s) {
+static cudaError_t launch_rho_jm(const RhoTask<T, TOUT>& tk, size_t smem, int64_t nblocks, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_rho_pairs<T, JM, TOUT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t nblocks = (int64_t)g.nk * g.Nn * ((g.Nm + JM - 1) / JM);
   if (nblocks > 0x7fffffff) return cudaErrorInvalidValue;
-  k_rho_pairs<T, JM, TOUT><<<(unsigned)nblocks, kRhoThreads, smem, s>>>(g, sm, U, kq, g0, gresp, gperm, tw1, tw2, R);
+  k_rho_pairs<T, JM, TOUT><<<(unsigned)nblocks, kRhoThreads, smem, s>>>(tk);
   return cudaGetLastError();
 }
 
 template <typename T, typename TOUT>
-cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
-                             const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
-                             const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
-                             cudaStream_t s) {
-  if (g.Nn <= 0 || g.Nm <= 0 || g.nk <= 0) return cudaSuccess;
+cudaError_t rho_task_make(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
+                          const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
+                          const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
+                          int jm_max, RhoTask<T, TOUT>* tk, size_t* smem, int64_t* nblocks) {
   if (g.Nn > 65535 || g.HX >= 32768 || g.HY * g.HZ >= 65536) return cudaErrorInvalidValue;
-  // zero padding below/above the n plane must cover every hz = G_z - G0z
   RhoSmem sm;
   // rows of the zero-padded n plane: row = padz + hz + b, b in [0, NZ), hz over
   // every tile of every k-pair: [Mz_lo - G0z_max, Mz_lo + nhb * kHZT - 1 - G0z_min]
@@ -412,20 +445,74 @@ cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const
   sm.padz = max(0, -hz_min);
   sm.unp_rows = max(sm.padz + hz_max + g.NZ, sm.padz + g.NZ);
   const int cap = kRhoThreads * kAccMax;
-  int jm = 4;
+  int jm = jm_max;
   while (jm > 1 && jm * g.ng > cap) jm /= 2;
   if (jm * g.ng > cap) return cudaErrorInvalidValue;  // ng > 4096
-  size_t smem = rho_smem_bytes<T>(g, sm, jm);
-  while (smem > 227 * 1024 && jm > 1) {
-    jm /= 2;
-    smem = rho_smem_bytes<T>(g, sm, jm);
+  *smem = rho_smem_bytes<T>(g, sm, jm_max);
+  tk->g = g;
+  tk->sm = sm;
+  tk->U = U;
+  tk->kq = kq;
+  tk->g0 = g0;
+  tk->gresp = gresp;
+  tk->gperm = gperm;
+  tk->tw1 = tw1;
+  tk->tw2 = tw2;
+  tk->R = R;
+  tk->jm = jm;
+  tk->block0 = 0;
+  *nblocks = (int64_t)g.nk * g.Nn * ((g.Nm + jm - 1) / jm);
+  return cudaSuccess;
+}
+
+template <typename T, typename TOUT>
+cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
+                             const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
+                             const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
+                             cudaStream_t s) {
+  if (g.Nn <= 0 || g.Nm <= 0 || g.nk <= 0) return cudaSuccess;
+  for (int jm : {4, 2, 1}) {
+    RhoTask<T, TOUT> tk;
+    size_t smem = 0;
+    int64_t nb = 0;
+    cudaError_t e = rho_task_make<T, TOUT>(g, U, kq, g0, gresp, gperm, tw1, tw2, R, jm, &tk, &smem, &nb);
+    if (e != cudaSuccess) return e;
+    if (tk.jm != jm || smem > 227 * 1024) continue;
+    switch (jm) {
+      case 4: return launch_rho_jm<T, 4, TOUT>(tk, smem, nb, s);
+      case 2: return launch_rho_jm<T, 2, TOUT>(tk, smem, nb, s);
+      default: return launch_rho_jm<T, 1, TOUT>(tk, smem, nb, s);
+    }
   }
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, typename TOUT>
+cudaError_t launch_rho_batch(const RhoTask<T, TOUT>* tasks_dev, int ntasks, int64_t total, int jm,
+                             size_t smem, unsigned long long* counter, int nsm, cudaStream_t s) {
+  if (ntasks == 0 || total == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  const int grid = nsm * 2;
+  (void)per_sm;
   switch (jm) {
-    case 4: return launch_rho_jm<T, 4, TOUT>(g, sm, smem, U, kq, g0, gresp, gperm, tw1, tw2, R, s);
-    case 2: return launch_rho_jm<T, 2, TOUT>(g, sm, smem, U, kq, g0, gresp, gperm, tw1, tw2, R, s);
-    default: return launch_rho_jm<T, 1, TOUT>(g, sm, smem, U, kq, g0, gresp, gperm, tw1, tw2, R, s);
+    case 4:
+      e = cudaFuncSetAttribute(k_rho_batch<T, 4, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_rho_batch<T, 4, TOUT><<<grid, kRhoThreads, smem, s>>>(tasks_dev, ntasks, total, counter);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(k_rho_batch<T, 2, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_rho_batch<T, 2, TOUT><<<grid, kRhoThreads, smem, s>>>(tasks_dev, ntasks, total, counter);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_rho_batch<T, 1, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_rho_batch<T, 1, TOUT><<<grid, kRhoThreads, smem, s>>>(tasks_dev, ntasks, total, counter);
   }
+  return cudaGetLastError();
 }
 
 template cudaError_t launch_wf_to_mixed<double>(const RhoGeom&, const int32_t*, const int32_t*,
@@ -434,6 +521,18 @@ template cudaError_t launch_wf_to_mixed<double>(const RhoGeom&, const int32_t*, 
 template cudaError_t launch_wf_to_mixed<float>(const RhoGeom&, const int32_t*, const int32_t*,
                                                const float2*, const float2*, const float2*,
                                                float2*, cudaStream_t);
+template cudaError_t rho_task_make<double, double2>(const RhoGeom&, const double2*, const int32_t*,
+                                                    const int32_t*, const int32_t*, const int32_t*,
+                                                    const double2*, const double2*, double2*, int,
+                                                    RhoTask<double, double2>*, size_t*, int64_t*);
+template cudaError_t rho_task_make<float, float2>(const RhoGeom&, const float2*, const int32_t*,
+                                                  const int32_t*, const int32_t*, const int32_t*,
+                                                  const float2*, const float2*, float2*, int,
+                                                  RhoTask<float, float2>*, size_t*, int64_t*);
+template cudaError_t launch_rho_batch<double, double2>(const RhoTask<double, double2>*, int, int64_t, int,
+                                                       size_t, unsigned long long*, int, cudaStream_t);
+template cudaError_t launch_rho_batch<float, float2>(const RhoTask<float, float2>*, int, int64_t, int,
+                                                     size_t, unsigned long long*, int, cudaStream_t);
 template cudaError_t launch_rho_pairs<double, double2>(const RhoGeom&, const double2*,
                                                        const int32_t*, const int32_t*,
                                                        const int32_t*, const int32_t*,

@@ -435,8 +435,9 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
 
 struct TcState {
   DevBuf ah, al, bh, bl, part;
+  CUtensorMap m_ah, m_al, m_bh, m_bl;
   int64_t kpad = 0;
-  int mpad = 0;
+  int mpad = 0, ntiles = 0, total_kb = 0, kbpc = 0, nchunks = 0;
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -467,15 +468,14 @@ bool make_map(CUtensorMap* m, void* ptr, int64_t kpad, int mpad) {
 
 }  // namespace
 
-chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
-                          double2* chi) {
+chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   if (!c->tc) c->tc = new TcState();
   TcState& t = *static_cast<TcState*>(c->tc);
   t.mpad = (2 * ng + kBM - 1) / kBM * kBM;
   t.kpad = (nt + kBK - 1) / kBK * kBK;
   const int nT = t.mpad / kBM;
-  const int ntiles = nT * (nT + 1) / 2;
-  const int total_kb = (int)(t.kpad / kBK);
+  t.ntiles = nT * (nT + 1) / 2;
+  t.total_kb = (int)(t.kpad / kBK);
   // split the transitions so that the grid fills whole waves of one CTA per SM
   int nsm = 148;
   {
@@ -487,9 +487,9 @@ chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t n
   int nsplit = 1;
   double best = 1e30;
   for (int sp = 1; sp <= 64; ++sp) {
-    const int kbps = (total_kb + sp - 1) / sp;
+    const int kbps = (t.total_kb + sp - 1) / sp;
     if (sp > 1 && kbps < 8 * kSubKB) break;  // keep every CTA busy for a while
-    const int ctas = ntiles * sp;
+    const int ctas = t.ntiles * sp;
     const int waves = (ctas + nsm - 1) / nsm;
     // time ~ waves * work per CTA; prefer fewer partials on ties
     const double cost = (double)waves * kbps + 4.0 * sp;
@@ -498,26 +498,33 @@ chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t n
       nsplit = sp;
     }
   }
-  const int kbpc = (total_kb + nsplit - 1) / nsplit;
-  const int nchunks = (total_kb + kbpc - 1) / kbpc;
+  t.kbpc = (t.total_kb + nsplit - 1) / nsplit;
+  t.nchunks = (t.total_kb + t.kbpc - 1) / t.kbpc;
+  if (t.kpad / kPT > 0x7fffffff / t.mpad)
+    return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
   const size_t opb = (size_t)t.mpad * t.kpad * 2;
   chi0_status s;
   if ((s = ctx_ensure(c, t.ah, opb, "A hi")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.al, opb, "A lo")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
-  if ((s = ctx_ensure(c, t.part, (size_t)nchunks * ntiles * (kBM / 2) * (kBN / 2) * 16,
+  if ((s = ctx_ensure(c, t.part, (size_t)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16,
                       "chunk partials")) != CHI0_OK)
     return s;
-  CUtensorMap m_ah, m_al, m_bh, m_bl;
-  if (!make_map(&m_ah, t.ah.p, t.kpad, t.mpad) || !make_map(&m_al, t.al.p, t.kpad, t.mpad) ||
-      !make_map(&m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&m_bl, t.bl.p, t.kpad, t.mpad))
+  if (!make_map(&t.m_ah, t.ah.p, t.kpad, t.mpad) || !make_map(&t.m_al, t.al.p, t.kpad, t.mpad) ||
+      !make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
     return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
+  return CHI0_OK;
+}
+
+chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
+                      double2* chi) {
+  if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "tensor-core contraction not planned");
+  TcState& t = *static_cast<TcState*>(c->tc);
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
-  if (t.kpad / kPT > 0x7fffffff / t.mpad) return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
   const int64_t n2 = (int64_t)ng * ng;
   // B = rho (frequency independent)
   stage_begin(c, CHI0_STAGE_WEIGHTS);
@@ -530,23 +537,24 @@ chi0_status tc_build_chi0(chi0_ctx* c, const void* R, const double* w, int64_t n
                                      (__nv_bfloat16*)t.ah.p, (__nv_bfloat16*)t.al.p);
     stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     stage_begin(c, CHI0_STAGE_CONTRACT);
-    k_herk_bf16x3<<<dim3(ntiles, nchunks), kThreads, kSmemBytes, c->st>>>(
-        m_ah, m_al, m_bh, m_bl, total_kb, kbpc, t.mpad, (double2*)t.part.p, ntiles, (int*)c->d_err.p);
+    k_herk_bf16x3<<<dim3(t.ntiles, t.nchunks), kThreads, kSmemBytes, c->st>>>(
+        t.m_ah, t.m_al, t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
+        (int*)c->d_err.p);
     stage_end(c, CHI0_STAGE_CONTRACT, 1);
     stage_begin(c, CHI0_STAGE_REDUCE);
     k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
-        (const double2*)t.part.p, nchunks, ntiles, ng, chi + (size_t)iw * n2);
+        (const double2*)t.part.p, t.nchunks, t.ntiles, ng, chi + (size_t)iw * n2);
     stage_end(c, CHI0_STAGE_REDUCE, 1);
   }
   // operand split: R read, hi/lo written (B once, A per frequency)
   c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(nw + 1) * ((double)nt * ng * 8 + 4.0 * t.mpad * t.kpad);
   // contraction: each launch streams A and B (hi and lo) once and writes its chunk partials
   c->stage[CHI0_STAGE_CONTRACT].bytes =
-      (double)nw * (8.0 * t.mpad * t.kpad + (double)nchunks * ntiles * (kBM / 2) * (kBN / 2) * 16);
-  c->stage[CHI0_STAGE_REDUCE].bytes = (double)nw * ((double)nchunks * ntiles * (kBM / 2) * (kBN / 2) * 16 + n2 * 16);
+      (double)nw * (8.0 * t.mpad * t.kpad + (double)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16);
+  c->stage[CHI0_STAGE_REDUCE].bytes = (double)nw * ((double)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16 + n2 * 16);
   // tensor-core work actually issued: 3 BF16 products over the lower-triangle tiles
-  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)ntiles * (double)t.kpad * nw;
-  e = cudaGetLastError();
+  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)t.ntiles * (double)t.kpad * nw;
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
 }

@@ -321,9 +321,8 @@ void term_tables(chi0_ctx* c, int iq, std::vector<double>& qgn, std::vector<doub
 
 }  // namespace
 
-// features (and targets) into x / t for chi at the ctx's current q point
-chi0_status term_prepare(chi0_ctx* c, int iq, const double2* chi, const double2* full, float* x,
-                         float* t) {
+// tables of the feature normalisation for q point iq (host set-up)
+chi0_status term_tables_upload(chi0_ctx* c, int iq) {
   const int ng = c->cfg.ng, nw = c->cfg.nw;
   chi0_status s;
   if ((s = ctx_ensure(c, c->d_termq, (size_t)ng * 8, "terminator tables")) != CHI0_OK) return s;
@@ -331,13 +330,18 @@ chi0_status term_prepare(chi0_ctx* c, int iq, const double2* chi, const double2*
   if ((s = ctx_ensure(c, c->d_termc, 16, "terminator scale")) != CHI0_OK) return s;
   std::vector<double> qgn, wn;
   term_tables(c, iq, qgn, wn);
-  // the tables are small: staged through the context's pinned-free path
   if (cudaMemcpyAsync(c->d_termq.p, qgn.data(), ng * 8, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
       cudaMemcpyAsync(c->d_termw.p, wn.data(), nw * 8, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess) {
     cudaGetLastError();
     return ctx_fail(c, CHI0_ECUDA, "terminator tables upload failed");
   }
+  return CHI0_OK;
+}
+
+// kernels: scale c, features (and targets) of chi
+chi0_status term_features_launch(chi0_ctx* c, const double2* chi, const double2* full, float* x, float* t) {
+  const int ng = c->cfg.ng, nw = c->cfg.nw;
   k_diag_scale<<<1, 256, 0, c->st>>>(chi, ng, (double*)c->d_termc.p);
   const int64_t n = (int64_t)ng * ng * nw;
   k_term_features_dev<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(
@@ -347,14 +351,20 @@ chi0_status term_prepare(chi0_ctx* c, int iq, const double2* chi, const double2*
   return CHI0_OK;
 }
 
-// chi += Hermitised network correction (build_chi0 with a terminator set)
-chi0_status term_apply_ctx(chi0_ctx* c, int iq, double2* chi) {
-  const int ng = c->cfg.ng, nw = c->cfg.nw;
-  const int64_t n = (int64_t)ng * ng * nw;
+chi0_status term_plan(chi0_ctx* c, int iq) {
+  const int64_t n = (int64_t)c->cfg.ng * c->cfg.ng * c->cfg.nw;
   chi0_status s;
   if ((s = ctx_ensure(c, c->d_termx, (size_t)n * kI * 4, "terminator features")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, c->d_termy, (size_t)n * kO * 4, "terminator prediction")) != CHI0_OK) return s;
-  if ((s = term_prepare(c, iq, chi, nullptr, (float*)c->d_termx.p, nullptr)) != CHI0_OK) return s;
+  return term_tables_upload(c, iq);
+}
+
+// chi += Hermitised network correction (build_chi0 with a terminator set)
+chi0_status term_launch(chi0_ctx* c, double2* chi) {
+  const int ng = c->cfg.ng, nw = c->cfg.nw;
+  const int64_t n = (int64_t)ng * ng * nw;
+  chi0_status s;
+  if ((s = term_features_launch(c, chi, nullptr, (float*)c->d_termx.p, nullptr)) != CHI0_OK) return s;
   if (mlp_predict(c->term_params, (const float*)c->d_termx.p, n, c->term_bf16, (float*)c->d_termy.p,
                   c->st) != cudaSuccess) {
     cudaGetLastError();
@@ -363,6 +373,7 @@ chi0_status term_apply_ctx(chi0_ctx* c, int iq, double2* chi) {
   k_term_apply_dev<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(chi, (const float*)c->d_termy.p, ng, nw,
                                                                    (const double*)c->d_termc.p);
   if (cudaGetLastError() != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, "terminator apply launch failed");
+  c->launches += 4;
   return CHI0_OK;
 }
 
@@ -417,7 +428,9 @@ chi0_status chi0_term_features(chi0_ctx* c, int iq, const void* chi_trunc, const
     return chi0::ctx_fail(c, CHI0_EINVAL, "bad iq or NULL buffer");
   if (c->h_gresp.empty() || c->rho_iq != iq)
     return chi0::ctx_fail(c, CHI0_ESTATE, "chi0_compute_rho(iq) must come first (response G set)");
-  chi0_status s = chi0::term_prepare(c, iq, (const double2*)chi_trunc, (const double2*)chi_full, x, t);
+  chi0_status s = chi0::term_tables_upload(c, iq);
+  if (s != CHI0_OK) return s;
+  s = chi0::term_features_launch(c, (const double2*)chi_trunc, (const double2*)chi_full, x, t);
   if (s != CHI0_OK) return s;
   if (scale) {
     double cs[2];
