@@ -35,7 +35,7 @@ def _systems(coef_dtype):
     spec = cfg_tiny(seed=63, kgrid=(2, 2, 2), q_frac=((0.5, 0.5, 0.0),), fft=(16, 16, 16), ng=30,
                     n_occ=4, n_bands=10, npw_target=40, a=7.0, freqs=(0.01j, 0.1j, 0.5j, 2.0j),
                     eta=0.0, coef_dtype=coef_dtype)
-    spec = dataclasses.replace(spec, occ_ev=(-10.0, 0.4), emp_ev=(-0.4, 30.0), kT_ev=0.05, n_electrons=8)
+    spec = dataclasses.replace(spec, occ_ev=(-2.0, 0.5), emp_ev=(-0.5, 4.0), kT_ev=0.05, n_electrons=8)
     metal = make_system(spec)
     return [(a, 0), (b, 0), (b, 1), (metal, 0)]
 
