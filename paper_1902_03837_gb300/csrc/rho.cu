@@ -221,15 +221,23 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
     twy[hyr * N2P + y] = tw2[pmod((hy_base + hyr) * y, N2)];
   }
 
-  // register accumulators: entry e <-> (j, i) = divmod(tid + e * threads, ng)
+  // register accumulators: entry e <-> (j, i) = divmod(tid + e * threads, ng);
+  // ent[e] packs its ys offset (low 20 bits) and x-twiddle row (high bits), or -1
   T2 acc[kAccMax];
-  int ent_j[kAccMax], ent_i[kAccMax];
+  int ent[kAccMax];
+  __syncthreads();  // gtab ready
 #pragma unroll
   for (int e = 0; e < kAccMax; ++e) {
     acc[e] = czero<T2>();
     const int idx = tid + e * kRhoThreads;
-    ent_j[e] = idx / g.ng;
-    ent_i[e] = idx - ent_j[e] * g.ng;
+    const int j = idx / g.ng;
+    const int i = idx - j * g.ng;
+    if (j < cm) {
+      const int gt = gtab[i];
+      ent[e] = ((gt >> 16) << 20) | (j * HY * HZ + (gt & 0xffff));
+    } else {
+      ent[e] = -1;
+    }
   }
 
   const T2* Un = U + ((size_t)ik * g.nb + (g.n_lo + nrel)) * ((size_t)g.N1 * plane);
@@ -267,17 +275,32 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
 #pragma unroll
         for (int h = 0; h < kHZT; ++h) a[j][h] = czero<T2>();
       // row of U_n(b + hz) in the padded array: b + hz + Lz + padz (b from -Lz)
-      const T2* un0 = unp + (size_t)(sm.padz + hz_base + hb * kHZT) * N2 + y;
-      for (int b = 0; b < NZ; ++b) {
-        T2 um[JM], un[kHZT];
+      const T2* pn = unp + (size_t)(sm.padz + hz_base + hb * kHZT) * N2 + y;
+      const T2* pm = ums + y;
+      if (cm == JM) {
+        for (int b = 0; b < NZ; ++b, pn += N2, pm += N2) {
+          T2 um[JM], un[kHZT];
 #pragma unroll
-        for (int j = 0; j < JM; ++j) um[j] = (j < cm) ? ums[((size_t)j * NZ + b) * N2 + y] : czero<T2>();
+          for (int j = 0; j < JM; ++j) um[j] = pm[j * (int)plane];
 #pragma unroll
-        for (int h = 0; h < kHZT; ++h) un[h] = un0[(size_t)(b + h) * N2];
+          for (int h = 0; h < kHZT; ++h) un[h] = pn[h * N2];
 #pragma unroll
-        for (int j = 0; j < JM; ++j)
+          for (int j = 0; j < JM; ++j)
 #pragma unroll
-          for (int h = 0; h < kHZT; ++h) cjmac(a[j][h], un[h], um[j]);
+            for (int h = 0; h < kHZT; ++h) cjmac(a[j][h], un[h], um[j]);
+        }
+      } else {
+        for (int b = 0; b < NZ; ++b, pn += N2, pm += N2) {
+          T2 um[JM], un[kHZT];
+#pragma unroll
+          for (int j = 0; j < JM; ++j) um[j] = (j < cm) ? pm[j * (int)plane] : czero<T2>();
+#pragma unroll
+          for (int h = 0; h < kHZT; ++h) un[h] = pn[h * N2];
+#pragma unroll
+          for (int j = 0; j < JM; ++j)
+#pragma unroll
+            for (int h = 0; h < kHZT; ++h) cjmac(a[j][h], un[h], um[j]);
+        }
       }
 #pragma unroll
       for (int h = 0; h < kHZT; ++h) {
@@ -309,11 +332,14 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       const T2* z1p = zs + ((size_t)j * HZ + hz1) * N2P;
       const int hy0 = yb * kHYT;
       const int ylo = half * yhalf, yhi = min(N2, ylo + yhalf);
+      const T2* tp[kHYT];
+#pragma unroll
+      for (int h = 0; h < kHYT; ++h) tp[h] = twy + (size_t)min(hy0 + h, HY - 1) * N2P;
       for (int y = ylo; y < yhi; ++y) {
         const T2 v0 = z0p[y], v1 = z1p[y];
 #pragma unroll
         for (int h = 0; h < kHYT; ++h) {
-          const T2 t = twy[(size_t)min(hy0 + h, HY - 1) * N2P + y];
+          const T2 t = tp[h][y];
           cmac(a[h][0], t, v0);
           cmac(a[h][1], t, v1);
         }
@@ -337,14 +363,13 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
     const T2* ys1 = ys + (size_t)JM * HY * HZ;
 #pragma unroll
     for (int e = 0; e < kAccMax; ++e) {
-      if (ent_j[e] < cm) {
-        const int gt = gtab[ent_i[e]];
-        const size_t o = (size_t)ent_j[e] * HY * HZ + (gt & 0xffff);
+      if (ent[e] >= 0) {
+        const int o = ent[e] & 0xfffff;
         T2 v = ys[o];
         const T2 v1 = ys1[o];
         v.x += v1.x;
         v.y += v1.y;
-        cmac(acc[e], tx[gt >> 16], v);
+        cmac(acc[e], tx[ent[e] >> 20], v);
       }
     }
     cp_async_wait_all();
@@ -355,7 +380,12 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
   const int64_t tbase = ((int64_t)ik * g.Nn + nrel) * g.Nm + m0;
 #pragma unroll
   for (int e = 0; e < kAccMax; ++e) {
-    if (ent_j[e] < cm) store_out<T2, TOUT>(R + (tbase + ent_j[e]) * g.ng + gout[ent_i[e]], acc[e], scale);
+    if (ent[e] >= 0) {
+      const int idx = tid + e * kRhoThreads;
+      const int j = idx / g.ng;
+      const int i = idx - j * g.ng;
+      store_out<T2, TOUT>(R + (tbase + j) * g.ng + gout[i], acc[e], scale);
+    }
   }
 }
 
