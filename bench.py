@@ -4,7 +4,8 @@ One step = the whole path over one synthetic system resident in HBM:
 wavefunctions -> mixed grid, oscillator strengths rho for every transition,
 transition weights, the chi0 contraction for every frequency, and the FP64
 Dyson inversion eps~^-1 for every frequency (chi0_compute_rho +
-chi0_build_chi0 + chi0_invert_eps).
+chi0_build_invert, which runs chi0_build_chi0 and chi0_invert_eps as one
+pipeline).
 
 Workload (default): the mixed-precision configuration -- cubic cell a = 10
 bohr, 8x8x8 k grid, 16 occupied + 184 empty bands, ~2000 plane waves per
@@ -190,8 +191,7 @@ def run_ours(args, rank, world, dist):
 
     def step():
         ctx.compute_rho(0)
-        ctx.build_chi0(0, None)
-        ctx.invert_eps(0, inv_d)
+        ctx.build_invert(0, inv_d)
 
     for _ in range(args.warmup):
         step()
@@ -239,8 +239,7 @@ def run_ours(args, rank, world, dist):
             ctx.set_wavefunctions(ik, pin_gv[ik], pin_cf[ik])
         ctx.set_energies(s.eps, s.occ)
         ctx.compute_rho(0)
-        ctx.build_chi0(0, None)
-        ctx.invert_eps(0, out_h)   # device -> host copy of the result, synchronises
+        ctx.build_invert(0, out_h)   # device -> host copy of the result, synchronises
 
     e2e_step()
     e2e_steps = max(1, min(args.steps, 3))

@@ -146,6 +146,22 @@ chi0_status chi0_build_chi0(chi0_ctx* ctx, int iq, void* out, int out_on_device)
  * CHI0_ENOTPD, CHI0_ENOMEM, CHI0_ECUDA. */
 chi0_status chi0_invert_eps(chi0_ctx* ctx, int iq, void* out, int out_on_device);
 
+/* chi0_build_chi0 followed by chi0_invert_eps (Eqs. chi0_def, X_rpa_inv, in
+ * the symmetric form of Eq. W_def) as one pipelined call: in the mixed form
+ * the Dyson step of frequency w runs on the FP64 units while the tensor-core
+ * contraction of the later frequencies proceeds (two internal streams forked
+ * from and joined back into the context's stream, the Dyson step at the
+ * higher priority).  In FP64 mode, or with a terminator set, the two steps run
+ * one after the other.  The results equal those of the two separate calls.
+ *   eps_out: [nw][ng][ng] complex128, receives eps~^-1 (NULL not allowed);
+ *   chi_out: NULL, or [nw][ng][ng] complex128 receiving chi0 (it also stays
+ *            on the device for a later chi0_invert_eps);
+ *   out_on_device: both outputs are device (1) or host (0) buffers; with host
+ *            buffers the call synchronises.
+ * Requires chi0_compute_rho(iq).  Errors: as chi0_build_chi0 and
+ * chi0_invert_eps. */
+chi0_status chi0_build_invert(chi0_ctx* ctx, int iq, void* chi_out, void* eps_out, int out_on_device);
+
 /* The response G vectors used at q index iq, out: [ng][3] int32 (host).
  * Errors: CHI0_EINVAL. */
 chi0_status chi0_get_response_gvectors(chi0_ctx* ctx, int iq, int32_t* out);

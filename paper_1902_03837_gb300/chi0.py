@@ -25,7 +25,7 @@ STATUS = {
 
 EXPORTS = (
     "chi0_create", "chi0_set_wavefunctions", "chi0_set_energies", "chi0_compute_rho",
-    "chi0_build_chi0", "chi0_invert_eps", "chi0_get_response_gvectors", "chi0_get_transitions",
+    "chi0_build_chi0", "chi0_invert_eps", "chi0_build_invert", "chi0_get_response_gvectors", "chi0_get_transitions",
     "chi0_get_rho", "chi0_get_rho_rows", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator",
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_compute_rho.argtypes = [P, I]
     lib.chi0_build_chi0.argtypes = [P, I, P, I]
     lib.chi0_invert_eps.argtypes = [P, I, P, I]
+    lib.chi0_build_invert.argtypes = [P, I, P, P, I]
     lib.chi0_get_response_gvectors.argtypes = [P, I, P]
     lib.chi0_get_transitions.argtypes = [P, ctypes.POINTER(I64), P]
     lib.chi0_get_rho.argtypes = [P, P]
@@ -303,6 +304,18 @@ class Chi0:
         p, dev = _ptr(out)
         self._check(_lib.chi0_invert_eps(self.h, int(iq), p, dev))
         return out
+
+    def build_invert(self, iq, eps_out, chi_out=None):
+        """chi0_build_invert: chi0 and eps~^-1 in one pipelined call.  eps_out
+        (and chi_out, if given) are both numpy arrays or both device tensors."""
+        p, dev = _ptr(eps_out)
+        cp = None
+        if chi_out is not None:
+            cp, cdev = _ptr(chi_out)
+            if cdev != dev:
+                raise ValueError("chi_out and eps_out must both be host or both be device buffers")
+        self._check(_lib.chi0_build_invert(self.h, int(iq), cp, p, dev))
+        return eps_out
 
     def get_response_gvectors(self, iq):
         out = np.zeros((self.ng, 3), dtype=np.int32)

@@ -299,8 +299,7 @@ chi0_status chi0_batch_run(chi0_batch* b, void* stream) {
     for (size_t i = 0; i < b->items.size() && s == CHI0_OK; ++i) {
       chi0_ctx* c = b->items[i];
       c->rho_iq = c->plan_rho_iq;
-      if ((s = chi0::launch_chi0(c)) != CHI0_OK) break;
-      if (b->outs[i]) s = chi0::launch_eps(c);
+      s = b->outs[i] ? chi0::launch_chi0_eps(c) : chi0::launch_chi0(c);
     }
     join(ns);
     cudaGraph_t g = nullptr;
@@ -312,7 +311,8 @@ chi0_status chi0_batch_run(chi0_batch* b, void* stream) {
       return s != CHI0_OK ? s : CHI0_ECUDA;
     }
     b->graph = g;
-    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    // node priorities let the overlapped Dyson step go ahead of the contraction
+    if (cudaGraphInstantiateWithFlags(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
       cudaGetLastError();
       return CHI0_ECUDA;
     }

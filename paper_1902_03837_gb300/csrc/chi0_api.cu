@@ -418,7 +418,7 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
 }
 
 // kernels of build_chi0 (weights, contraction, reduction, terminator)
-chi0_status launch_chi0(chi0_ctx* c) {
+chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq) {
   const int iq = c->plan_chi_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "chi0 not planned");
   const int nw = c->cfg.nw, ng = c->cfg.ng;
@@ -455,7 +455,8 @@ chi0_status launch_chi0(chi0_ctx* c) {
       chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
       c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
     } else {
-      s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p);
+      s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p,
+                          c->term_params ? nullptr : ev_freq);
       if (s != CHI0_OK) return s;
     }
     if (c->term_params) {
@@ -491,6 +492,24 @@ chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
   }
   CK(cudaMemcpyAsync(c->d_vsqrt.p, v.data(), ng * 8, cudaMemcpyHostToDevice, c->st), "v H2D");
   CK(cudaStreamSynchronize(c->st), "synchronize");
+  CK(chi0::dyson_prepare(), "Dyson kernel attributes");
+  if (!c->s_ct) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+    // The Dyson blocks go first whenever they are pending: blocks of a
+    // lower-priority grid are only dispatched while no higher-priority block
+    // waits, so at the lower priority the Dyson step would run only in the
+    // gaps between contraction launches.
+    CK(cudaStreamCreateWithPriority(&c->s_ct, cudaStreamNonBlocking, least), "pipeline stream");
+    CK(cudaStreamCreateWithPriority(&c->s_dy, cudaStreamNonBlocking, greatest), "pipeline stream");
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join_ct, &c->ev_join_dy};
+    for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "pipeline event");
+  }
+  while ((int)c->ev_freq.size() < nw) {
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "pipeline event");
+    c->ev_freq.push_back(e);
+  }
   c->plan_eps_out = A;
   c->plan_eps_iq = iq;
   return CHI0_OK;
@@ -510,6 +529,57 @@ chi0_status launch_eps(chi0_ctx* c) {
   chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * ((ng + 31) / 32));
   // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency (about
   // half of them executed, the Hermitian lower tiles)
+  c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
+  c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
+  c->eps_iq = iq;
+  return CHI0_OK;
+}
+
+chi0_status launch_chi0_eps(chi0_ctx* c) {
+  const int iq = c->plan_chi_iq;
+  if (iq < 0 || c->plan_eps_iq != iq) return fail(c, CHI0_ESTATE, "build and Dyson step not planned");
+  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  chi0_status s;
+  if (c->fp64 || c->term_params || c->nt == 0 || nw < 2) {
+    // FP64 contraction and Dyson share the FP64 pipe; the terminator needs
+    // every frequency of chi0 first: no overlap to gain
+    if ((s = launch_chi0(c)) != CHI0_OK) return s;
+    return launch_eps(c);
+  }
+  const size_t n2 = (size_t)ng * ng;
+  cudaStream_t base = c->st;
+  cudaEventRecord(c->ev_fork, base);
+  cudaStreamWaitEvent(c->s_ct, c->ev_fork, 0);
+  cudaStreamWaitEvent(c->s_dy, c->ev_fork, 0);
+  c->st = c->s_ct;
+  s = launch_chi0(c, c->ev_freq.data());
+  c->st = c->s_dy;
+  // Dyson steps in groups of 4 frequencies: the pivot-block inverses of a
+  // group run side by side (one SM each), which a single frequency's chain
+  // of 32 dependent pivot steps cannot hide.  The last four frequencies go
+  // as 2, 1, 1, so that after the last contraction only one frequency's
+  // Dyson step is left.
+  const int nT = (ng + 31) / 32;
+  for (int w0 = 0; w0 < nw && s == CHI0_OK;) {
+    const int r = nw - w0;
+    const int gw = r > 4 ? std::min(4, r - 4) : (r == 4 ? 2 : 1);
+    cudaStreamWaitEvent(c->s_dy, c->ev_freq[w0 + gw - 1], 0);
+    chi0::stage_begin(c, CHI0_STAGE_DYSON);
+    cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p + w0 * n2, (const double*)c->d_vsqrt.p,
+                                       ng, gw, c->plan_eps_out + w0 * n2, (double2*)c->d_colp.p,
+                                       (double2*)c->d_rowp.p, (double2*)c->d_pinv.p, (int*)c->d_err.p,
+                                       c->s_dy);
+    if (e != cudaSuccess) s = cuda_fail(c, e, "dyson launch");
+    chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * nT);
+    w0 += gw;
+  }
+  c->st = base;
+  // join (also on failure, so that a capture stays well formed)
+  cudaEventRecord(c->ev_join_ct, c->s_ct);
+  cudaEventRecord(c->ev_join_dy, c->s_dy);
+  cudaStreamWaitEvent(base, c->ev_join_ct, 0);
+  cudaStreamWaitEvent(base, c->ev_join_dy, 0);
+  if (s != CHI0_OK) return s;
   c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
   c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
   c->eps_iq = iq;
@@ -720,6 +790,32 @@ chi0_status chi0_invert_eps(chi0_ctx* c, int iq, void* out, int out_on_device) {
   return CHI0_OK;
 }
 
+chi0_status chi0_build_invert(chi0_ctx* c, int iq, void* chi_out, void* eps_out, int out_on_device) {
+  if (!c) return CHI0_EINVAL;
+  if (iq != c->rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
+  if (!eps_out) return fail(c, CHI0_EINVAL, "NULL output");
+  const size_t bytes = (size_t)c->cfg.ng * c->cfg.ng * c->cfg.nw * 16;
+  chi0_status s;
+  double2* A;
+  if (out_on_device) {
+    A = (double2*)eps_out;
+  } else {
+    if ((s = ensure(c, c->d_A, bytes, "eps")) != CHI0_OK) return s;
+    A = (double2*)c->d_A.p;
+  }
+  if ((s = chi0::plan_chi0(c, iq)) != CHI0_OK) return s;
+  if ((s = chi0::plan_eps(c, iq, A)) != CHI0_OK) return s;
+  if ((s = chi0::launch_chi0_eps(c)) != CHI0_OK) return s;
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (chi_out) CK(cudaMemcpyAsync(chi_out, c->d_chi.p, bytes, kind, c->st), "chi0 copy out");
+  if (!out_on_device) {
+    CK(cudaMemcpyAsync(eps_out, A, bytes, cudaMemcpyDeviceToHost, c->st), "eps copy out");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    return check_device_error(c);
+  }
+  return CHI0_OK;
+}
+
 chi0_status chi0_get_response_gvectors(chi0_ctx* c, int iq, int32_t* out) {
   if (!c) return CHI0_EINVAL;
   if (iq < 0 || iq >= c->cfg.nq || !out) return fail(c, CHI0_EINVAL, "bad iq or NULL out");
@@ -842,6 +938,17 @@ void chi0_destroy(chi0_ctx* c) {
     for (cudaEvent_t e : st.ev)
       if (e) cudaEventDestroy(e);
   chi0::tc_release(c);
+  cudaStream_t pst[] = {c->s_ct, c->s_dy};
+  for (cudaStream_t t : pst)
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
+  cudaEvent_t pev[] = {c->ev_fork, c->ev_join_ct, c->ev_join_dy};
+  for (cudaEvent_t e : pev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_freq)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 

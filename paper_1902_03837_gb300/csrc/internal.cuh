@@ -106,5 +106,8 @@ cudaError_t launch_chi0_reduce(const double2* part, int nchunks, int ng, int nw,
 cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,
                          double2* colpanel, double2* rowpanel, double2* pinv, int* err_flag,
                          cudaStream_t s);
+// The Dyson kernels prefer the whole shared-memory carveout, the setting of
+// the tensor-core contraction, so that both can share an SM.
+cudaError_t dyson_prepare();
 
 }  // namespace chi0

@@ -516,12 +516,25 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
+  // The whole shared-memory carveout on every SM this path touches, so that
+  // an SM running a contraction CTA (193 KB) keeps room for the small blocks
+  // of the Dyson step of the previous frequency (a carveout sized to the CTA
+  // alone would leave none).
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_prep, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_reduce, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
 }
 
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
-                      double2* chi) {
+                      double2* chi, const cudaEvent_t* ev_freq) {
   if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "tensor-core contraction not planned");
   TcState& t = *static_cast<TcState*>(c->tc);
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
@@ -545,6 +558,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
     k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
         (const double2*)t.part.p, t.nchunks, t.ntiles, ng, chi + (size_t)iw * n2);
     stage_end(c, CHI0_STAGE_REDUCE, 1);
+    if (ev_freq) cudaEventRecord(ev_freq[iw], c->st);
   }
   // operand split: R read, hi/lo written (B once, A per frequency)
   c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(nw + 1) * ((double)nt * ng * 8 + 4.0 * t.mpad * t.kpad);

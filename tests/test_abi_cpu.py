@@ -37,6 +37,17 @@ def test_exports_match_header(binding):
     assert set(names) == set(binding.EXPORTS)
 
 
+def test_binding_declares_every_signature(binding):
+    """Every entry point with arguments has ctypes argtypes: an undeclared
+    pointer argument would be passed as a 32-bit int."""
+    import re
+    src = open(binding.__file__).read()
+    for n in binding.EXPORTS:
+        assert re.search(rf"lib\.{n}\.argtypes\s*=", src), n
+        fn = getattr(binding._lib, n)
+        assert fn.argtypes is not None, n
+
+
 def _ctx(binding, **over):
     kw = dict(a=10.0, kgrid=(4, 4, 4), nbands=32, npw_max=305, fft=(24, 24, 24), ng=59,
               q_frac=[(0.25, 0, 0)], omega=[0j], eta=0.1 / 27.211386245988)
