@@ -418,7 +418,7 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
 }
 
 // kernels of build_chi0 (weights, contraction, reduction, terminator)
-chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq) {
+chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep) {
   const int iq = c->plan_chi_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "chi0 not planned");
   const int nw = c->cfg.nw, ng = c->cfg.ng;
@@ -456,7 +456,7 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq) {
       c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
     } else {
       s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p,
-                          c->term_params ? nullptr : ev_freq);
+                          c->term_params ? nullptr : ev_freq, c->term_params ? nullptr : ev_prep);
       if (s != CHI0_OK) return s;
     }
     if (c->term_params) {
@@ -506,9 +506,11 @@ chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
     for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "pipeline event");
   }
   while ((int)c->ev_freq.size() < nw) {
-    cudaEvent_t e = nullptr;
+    cudaEvent_t e = nullptr, f = nullptr;
     CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "pipeline event");
     c->ev_freq.push_back(e);
+    CK(cudaEventCreateWithFlags(&f, cudaEventDisableTiming), "pipeline event");
+    c->ev_prep.push_back(f);
   }
   c->plan_eps_out = A;
   c->plan_eps_iq = iq;
@@ -552,7 +554,7 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
   cudaStreamWaitEvent(c->s_ct, c->ev_fork, 0);
   cudaStreamWaitEvent(c->s_dy, c->ev_fork, 0);
   c->st = c->s_ct;
-  s = launch_chi0(c, c->ev_freq.data());
+  s = launch_chi0(c, c->ev_freq.data(), c->ev_prep.data());
   c->st = c->s_dy;
   // Dyson steps in groups of 4 frequencies: the pivot-block inverses of a
   // group run side by side (one SM each), which a single frequency's chain
@@ -564,6 +566,10 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
     const int r = nw - w0;
     const int gw = r > 4 ? std::min(4, r - 4) : (r == 4 ? 2 : 1);
     cudaStreamWaitEvent(c->s_dy, c->ev_freq[w0 + gw - 1], 0);
+    // and, when a split pass follows, until it is done: the Dyson blocks then
+    // share the SMs with the (tensor-bound) contraction, not with the
+    // (bandwidth-bound) split
+    if (w0 + gw < nw) cudaStreamWaitEvent(c->s_dy, c->ev_prep[w0 + gw], 0);
     chi0::stage_begin(c, CHI0_STAGE_DYSON);
     cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p + w0 * n2, (const double*)c->d_vsqrt.p,
                                        ng, gw, c->plan_eps_out + w0 * n2, (double2*)c->d_colp.p,
@@ -948,6 +954,8 @@ void chi0_destroy(chi0_ctx* c) {
   for (cudaEvent_t e : pev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_freq)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_prep)
     if (e) cudaEventDestroy(e);
   delete c;
 }

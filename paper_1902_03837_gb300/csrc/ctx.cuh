@@ -71,6 +71,7 @@ struct chi0_ctx {
   // (highest priority), both forked from and joined back into st
   cudaStream_t s_ct = nullptr, s_dy = nullptr;
   std::vector<cudaEvent_t> ev_freq;  // [nw] contraction (and reduction) of frequency w done
+  std::vector<cudaEvent_t> ev_prep;  // [nw] operand split of frequency w done
   cudaEvent_t ev_fork = nullptr, ev_join_ct = nullptr, ev_join_dy = nullptr;
 };
 
@@ -86,9 +87,11 @@ void stage_end(chi0_ctx* c, int stage, int kernels);
 // split-precision tensor-core contraction (mixed mode): chi[iw][i][j] from
 // R (complex64 [nt][ng]) and real weights w[iw][t]
 chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw);
-// ev_freq (optional, [nw]): event w is recorded once chi of frequency w is final
+// ev_freq (optional, [nw]): event w is recorded once chi of frequency w is final;
+// ev_prep (optional, [nw]): event w once the operand of frequency w is split
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
-                      double2* chi, const cudaEvent_t* ev_freq = nullptr);
+                      double2* chi, const cudaEvent_t* ev_freq = nullptr,
+                      const cudaEvent_t* ev_prep = nullptr);
 void tc_release(chi0_ctx* c);
 // learned terminator: network kernels and the correction of a built chi0
 int mlp_nparams();
@@ -101,7 +104,8 @@ chi0_status term_launch(chi0_ctx* c, double2* chi);
 chi0_status plan_rho(chi0_ctx* c, int iq);
 chi0_status launch_rho(chi0_ctx* c, bool with_pairs);
 chi0_status plan_chi0(chi0_ctx* c, int iq);
-chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq = nullptr);
+chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq = nullptr,
+                        const cudaEvent_t* ev_prep = nullptr);
 chi0_status plan_eps(chi0_ctx* c, int iq, double2* A);
 chi0_status launch_eps(chi0_ctx* c);
 // build_chi0 and invert_eps as one pipeline: the Dyson step of frequency w

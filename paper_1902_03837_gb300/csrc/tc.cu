@@ -192,17 +192,26 @@ __device__ __forceinline__ void nsum(float& s, float& c, float x) {
   s = t;
 }
 
-// One CTA = one lower-triangle tile (I, J) x one range of k-blocks.  The MMA
-// thread alternates between two TMEM accumulators, one per sub-chunk of
-// kSubKB k-blocks; the epilogue warps drain a finished sub-chunk (complex
+// Work unit = one lower-triangle tile (I, J) x one range of k-blocks (a
+// split); unit u is tile u % ntiles of split u / ntiles, so the CTAs resident
+// at one time read the same k-blocks (shared in L2).  The kernel is
+// persistent: CTA c takes units c, c + gridDim.x, ...; the stage ring and the
+// accumulator ping-pong run on across units, so the next unit's operands
+// stream in while the epilogue finishes the last one, and the CTA holds its SM
+// for the whole launch (blocks of a concurrent kernel fill what it leaves).
+// The MMA thread alternates between two TMEM accumulators, one per sub-chunk
+// of kSubKB k-blocks; the epilogue warps drain a finished sub-chunk (complex
 // combination, compensated FP32 sums held in registers) while the other one
 // fills, so the tensor core's FP32 accumulation never runs longer than
 // kSubKB * 64 transitions.
-__global__ void __launch_bounds__(kThreads, 1)
+// At most 224 registers: two warps of this CTA share a sub-partition, and
+// 2 x 224 x 32 leaves 2048 of its 16384 registers for a 64-register warp of
+// a concurrent Dyson block.
+__global__ void __maxnreg__(224)
 k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
               int total_kb, int kb_per_split, int mpad, double2* __restrict__ part, int ntiles,
-              int* __restrict__ err) {
+              int nunits, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -216,14 +225,12 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, split = blockIdx.y;
   if (*(volatile int*)(err + 1)) return;  // an earlier CTA timed out: skip the work
-  int I, J;
-  tri_decode(tile, I, J);
-  const int kb0 = split * kb_per_split;
-  const int kb1 = min(total_kb, kb0 + kb_per_split);
-  const int nkb = max(0, kb1 - kb0);
-  const int nsub = (nkb + kSubKB - 1) / kSubKB;
+  // k-block range of a unit
+  auto unit_range = [&](int u, int& kb0, int& nkb) {
+    kb0 = (u / ntiles) * kb_per_split;
+    nkb = max(0, min(total_kb, kb0 + kb_per_split) - kb0);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -252,100 +259,125 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      for (int k = 0; k < nkb; ++k) {
-        const int s = k % kStages;
-        const uint32_t ph = (uint32_t)((k / kStages) & 1);
-        if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, err)) break;
-        const uint32_t st = base + s * kStageBytes;
-        mbar_expect_tx(bar_full + 8 * s, kStageBytes);
-        const int row = (kb0 + k) * mpad;  // k-blocked layout: block kb starts at row kb * mpad
-        tma_load_2d(st, &tm_ah, 0, row + I * kBM, bar_full + 8 * s);
-        tma_load_2d(st + kTileBytes, &tm_al, 0, row + I * kBM, bar_full + 8 * s);
-        tma_load_2d(st + 2 * kTileBytes, &tm_bh, 0, row + J * kBN, bar_full + 8 * s);
-        tma_load_2d(st + 3 * kTileBytes, &tm_bl, 0, row + J * kBN, bar_full + 8 * s);
+      int gk = 0;  // k-blocks loaded by this CTA so far (stage ring position)
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int I, J, kb0, nkb;
+        tri_decode(u % ntiles, I, J);
+        unit_range(u, kb0, nkb);
+        for (int k = 0; k < nkb; ++k, ++gk) {
+          const int s = gk % kStages;
+          const uint32_t ph = (uint32_t)((gk / kStages) & 1);
+          if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + s * kStageBytes;
+          mbar_expect_tx(bar_full + 8 * s, kStageBytes);
+          const int row = (kb0 + k) * mpad;  // k-blocked layout: block kb starts at row kb * mpad
+          tma_load_2d(st, &tm_ah, 0, row + I * kBM, bar_full + 8 * s);
+          tma_load_2d(st + kTileBytes, &tm_al, 0, row + I * kBM, bar_full + 8 * s);
+          tma_load_2d(st + 2 * kTileBytes, &tm_bh, 0, row + J * kBN, bar_full + 8 * s);
+          tma_load_2d(st + 3 * kTileBytes, &tm_bl, 0, row + J * kBN, bar_full + 8 * s);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(kBM, kBN);
-      int k = 0;
-      for (int sc = 0; sc < nsub; ++sc) {
-        const int b = sc & 1;
-        if (!mbar_wait(bar_acce + 8 * b, (uint32_t)(((sc >> 1) & 1) ^ 1), abort_flag, err)) break;
-        tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(b * kBN);
-        const int kend = min(nkb, (sc + 1) * kSubKB);
-        bool ok = true;
-        for (int kk0 = 0; k < kend; ++k, ++kk0) {
-          const int s = k % kStages;
-          const uint32_t ph = (uint32_t)((k / kStages) & 1);
-          if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, err)) {
+      int gk = 0, gsc = 0;  // stage ring position, sub-chunks issued by this CTA
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int kb0, nkb;
+        unit_range(u, kb0, nkb);
+        const int nsub = (nkb + kSubKB - 1) / kSubKB;
+        int k = 0;
+        for (int sc = 0; sc < nsub; ++sc, ++gsc) {
+          const int b = gsc & 1;
+          if (!mbar_wait(bar_acce + 8 * b, (uint32_t)(((gsc >> 1) & 1) ^ 1), abort_flag, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = base + s * kStageBytes;
-          const uint64_t dah = desc_sw128(st);
-          const uint64_t dal = desc_sw128(st + kTileBytes);
-          const uint64_t dbh = desc_sw128(st + 2 * kTileBytes);
-          const uint64_t dbl = desc_sw128(st + 3 * kTileBytes);
+          const uint32_t acc = tmem + (uint32_t)(b * kBN);
+          const int kend = min(nkb, (sc + 1) * kSubKB);
+          for (int kk0 = 0; k < kend; ++k, ++kk0, ++gk) {
+            const int s = gk % kStages;
+            const uint32_t ph = (uint32_t)((gk / kStages) & 1);
+            if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = base + s * kStageBytes;
+            const uint64_t dah = desc_sw128(st);
+            const uint64_t dal = desc_sw128(st + kTileBytes);
+            const uint64_t dbh = desc_sw128(st + 2 * kTileBytes);
+            const uint64_t dbl = desc_sw128(st + 3 * kTileBytes);
 #pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 BF16 = 32 bytes along K
-            umma_bf16(acc, dah + off, dbh + off, idesc, (kk0 > 0 || kk > 0) ? 1u : 0u);
-            umma_bf16(acc, dah + off, dbl + off, idesc, 1u);
-            umma_bf16(acc, dal + off, dbh + off, idesc, 1u);
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 16 BF16 = 32 bytes along K
+              umma_bf16(acc, dah + off, dbh + off, idesc, (kk0 > 0 || kk > 0) ? 1u : 0u);
+              umma_bf16(acc, dah + off, dbl + off, idesc, 1u);
+              umma_bf16(acc, dal + off, dbh + off, idesc, 1u);
+            }
+            umma_commit(bar_empty + 8 * s);  // stage free once these MMAs have read it
           }
-          umma_commit(bar_empty + 8 * s);  // stage free once these MMAs have read it
+          if (!ok) break;
+          umma_commit(bar_accf + 8 * b);     // sub-chunk sum ready in accumulator b
         }
-        if (!ok) break;
-        umma_commit(bar_accf + 8 * b);     // sub-chunk sum ready in accumulator b
       }
     }
   } else {
     // ---------------- epilogue (warps 2..5 -> TMEM lane quadrants 2, 3, 0, 1)
     const int q = warp & 3;
     const bool odd = (lane & 1) != 0;
-    float accs[32][2], accc[32][2];  // compensated sums: [complex entry][re, im]
-#pragma unroll
-    for (int e = 0; e < 32; ++e) accs[e][0] = accs[e][1] = accc[e][0] = accc[e][1] = 0.f;
+    int gsc = 0;  // sub-chunks drained by this CTA
     bool ok = true;
-    for (int sc = 0; sc < nsub; ++sc) {
-      const int b = sc & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * b, (uint32_t)((sc >> 1) & 1), abort_flag, err) ? 1 : 0) != 0;
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kBN);
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      int kb0, nkb;
+      unit_range(u, kb0, nkb);
+      const int nsub = (nkb + kSubKB - 1) / kSubKB;
+      float accs[32][2], accc[32][2];  // compensated sums: [complex entry][re, im]
 #pragma unroll
-      for (int cb = 0; cb < kBN / 16; ++cb) {
-        uint32_t v[16];
-        tmem_ld16(acc + (uint32_t)(cb * 16), v);
-        // rows 2i (even lane) and 2i+1 (odd lane); each lane combines 4 of the 8 complex columns
-        float recv[8];
+      for (int e = 0; e < 32; ++e) accs[e][0] = accs[e][1] = accc[e][0] = accc[e][1] = 0.f;
+      for (int sc = 0; sc < nsub; ++sc, ++gsc) {
+        const int b = gsc & 1;
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(bar_accf + 8 * b, (uint32_t)((gsc >> 1) & 1), abort_flag, err) ? 1 : 0) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kBN);
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) {
-          const float send = __uint_as_float(odd ? v[k2] : v[8 + k2]);
-          recv[k2] = __shfl_xor_sync(0xffffffffu, send, 1);
+        for (int cb = 0; cb < kBN / 16; ++cb) {
+          uint32_t v[16];
+          tmem_ld16(acc + (uint32_t)(cb * 16), v);
+          // rows 2i (even lane) and 2i+1 (odd lane); each lane combines 4 of the 8 complex columns
+          float recv[8];
+#pragma unroll
+          for (int k2 = 0; k2 < 8; ++k2) {
+            const float send = __uint_as_float(odd ? v[k2] : v[8 + k2]);
+            recv[k2] = __shfl_xor_sync(0xffffffffu, send, 1);
+          }
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const float r0c0 = odd ? recv[2 * jj] : __uint_as_float(v[2 * jj]);           // D[2i][2j]
+            const float r0c1 = odd ? recv[2 * jj + 1] : __uint_as_float(v[2 * jj + 1]);   // D[2i][2j+1]
+            const float r1c0 = odd ? __uint_as_float(v[8 + 2 * jj]) : recv[2 * jj];       // D[2i+1][2j]
+            const float r1c1 = odd ? __uint_as_float(v[9 + 2 * jj]) : recv[2 * jj + 1];   // D[2i+1][2j+1]
+            const int e = cb * 4 + jj;
+            nsum(accs[e][0], accc[e][0], r0c0 + r1c1);
+            nsum(accs[e][1], accc[e][1], r1c0 - r0c1);
+          }
         }
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const float r0c0 = odd ? recv[2 * jj] : __uint_as_float(v[2 * jj]);           // D[2i][2j]
-          const float r0c1 = odd ? recv[2 * jj + 1] : __uint_as_float(v[2 * jj + 1]);   // D[2i][2j+1]
-          const float r1c0 = odd ? __uint_as_float(v[8 + 2 * jj]) : recv[2 * jj];       // D[2i+1][2j]
-          const float r1c1 = odd ? __uint_as_float(v[9 + 2 * jj]) : recv[2 * jj + 1];   // D[2i+1][2j+1]
-          const int e = cb * 4 + jj;
-          nsum(accs[e][0], accc[e][0], r0c0 + r1c1);
-          nsum(accs[e][1], accc[e][1], r1c0 - r0c1);
-        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acce + 8 * b) : "memory");
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acce + 8 * b) : "memory");
-    }
-    if (ok) {
+      if (!ok) break;
       const int il = (q * 32 + lane) >> 1;  // complex row of the tile
-      double2* out = part + ((size_t)split * ntiles + tile) * (size_t)(kBM / 2) * (kBN / 2) +
+      double2* out = part + ((size_t)(u / ntiles) * ntiles + (u % ntiles)) * (size_t)(kBM / 2) * (kBN / 2) +
                      (size_t)il * (kBN / 2) + (odd ? 4 : 0);
 #pragma unroll
       for (int cb = 0; cb < kBN / 16; ++cb)
@@ -372,43 +404,50 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
 constexpr int kPT = 64;  // transitions per tile (= one k-block)
 constexpr int kPI = 32;  // complex G per tile
 
+// Up to kPrepGroup frequencies are split in one pass, so that R is read once
+// for all of them (the split is bound by HBM traffic: R in, hi/lo out).
+constexpr int kPrepGroup = 4;
+struct PrepOut {
+  __nv_bfloat16* hi[kPrepGroup];
+  __nv_bfloat16* lo[kPrepGroup];
+};
+
+// w: NULL (unit weights) or the weights of ngrp consecutive frequencies, w[g * nt + t]
 __global__ void __launch_bounds__(256)
-k_prep(const float2* __restrict__ R, const double* __restrict__ w, int64_t nt, int ng, int mpad,
-       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+k_prep(const float2* __restrict__ R, const double* __restrict__ w, int ngrp, int64_t nt, int ng,
+       int mpad, const __grid_constant__ PrepOut out) {
   __shared__ float tile[2 * kPI][kPT + 1];
-  __shared__ float ws[kPT];  // weights of the tile's transitions, converted once (FP64 is slow here)
+  __shared__ float ws[kPrepGroup][kPT];  // weights converted once per transition (FP64 is slow here)
   const int64_t kb = blockIdx.x;
   const int64_t t0 = kb * kPT;
   const int i0 = blockIdx.y * kPI;
-  if (threadIdx.x < kPT) {
-    const int64_t t = t0 + threadIdx.x;
-    ws[threadIdx.x] = (w && t < nt) ? (float)w[t] : 1.f;
+  for (int e = threadIdx.x; e < ngrp * kPT; e += 256) {
+    const int g = e / kPT, tl = e % kPT;
+    const int64_t t = t0 + tl;
+    ws[g][tl] = (w && t < nt) ? (float)w[(size_t)g * nt + t] : 1.f;
   }
-  __syncthreads();
   for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
     const int tl = e / kPI, il = e % kPI;
     const int64_t t = t0 + tl;
     const int i = i0 + il;
-    float2 v = make_float2(0.f, 0.f);
-    if (t < nt && i < ng) {
-      v = R[t * ng + i];
-      const float s = ws[tl];
-      v.x *= s;
-      v.y *= s;
-    }
+    const float2 v = (t < nt && i < ng) ? R[t * ng + i] : make_float2(0.f, 0.f);
     tile[2 * il][tl] = v.x;
     tile[2 * il + 1][tl] = v.y;
   }
   __syncthreads();
   const size_t blk = (size_t)kb * mpad * kPT;
-  for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
-    const int ml = e / (kPT / 2), tp = e % (kPT / 2);
-    const float x0 = tile[ml][2 * tp], x1 = tile[ml][2 * tp + 1];
-    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
-    const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
-    *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
-    *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+  for (int g = 0; g < ngrp; ++g) {
+    __nv_bfloat16* __restrict__ hi = out.hi[g];
+    __nv_bfloat16* __restrict__ lo = out.lo[g];
+    for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
+      const int ml = e / (kPT / 2), tp = e % (kPT / 2);
+      const float x0 = tile[ml][2 * tp] * ws[g][2 * tp], x1 = tile[ml][2 * tp + 1] * ws[g][2 * tp + 1];
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+      const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
+      *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+      *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+    }
   }
 }
 
@@ -434,10 +473,12 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
 }
 
 struct TcState {
-  DevBuf ah, al, bh, bl, part;
-  CUtensorMap m_ah, m_al, m_bh, m_bl;
+  DevBuf ah[kPrepGroup], al[kPrepGroup], bh, bl, part;
+  CUtensorMap m_ah[kPrepGroup], m_al[kPrepGroup], m_bh, m_bl;
   int64_t kpad = 0;
   int mpad = 0, ntiles = 0, total_kb = 0, kbpc = 0, nchunks = 0;
+  int group = 1;  // frequencies per operand-split pass (A buffers in use)
+  int nsm = 1;    // persistent contraction grid
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -484,6 +525,7 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
   }
+  t.nsm = nsm;
   int nsplit = 1;
   double best = 1e30;
   for (int sp = 1; sp <= 64; ++sp) {
@@ -504,15 +546,32 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
   const size_t opb = (size_t)t.mpad * t.kpad * 2;
   chi0_status s;
-  if ((s = ctx_ensure(c, t.ah, opb, "A hi")) != CHI0_OK) return s;
-  if ((s = ctx_ensure(c, t.al, opb, "A lo")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.part, (size_t)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16,
                       "chunk partials")) != CHI0_OK)
     return s;
-  if (!make_map(&t.m_ah, t.ah.p, t.kpad, t.mpad) || !make_map(&t.m_al, t.al.p, t.kpad, t.mpad) ||
-      !make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
+  // A buffers for up to kPrepGroup frequencies, as far as half of the free
+  // device memory allows (one pair is always needed)
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    int have = 0;
+    while (have < kPrepGroup && t.ah[have].bytes >= opb && t.al[have].bytes >= opb) ++have;
+    int g = std::min(kPrepGroup, std::max(1, nw));
+    while (g > std::max(1, have) && (double)(g - have) * 2.0 * (double)opb > 0.5 * (double)free_b) --g;
+    t.group = g;
+  }
+  for (int g = 0; g < t.group; ++g) {
+    if ((s = ctx_ensure(c, t.ah[g], opb, "A hi")) != CHI0_OK) return s;
+    if ((s = ctx_ensure(c, t.al[g], opb, "A lo")) != CHI0_OK) return s;
+    if (!make_map(&t.m_ah[g], t.ah[g].p, t.kpad, t.mpad) || !make_map(&t.m_al[g], t.al[g].p, t.kpad, t.mpad))
+      return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
+  }
+  if (!make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
     return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
@@ -534,34 +593,49 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
 }
 
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
-                      double2* chi, const cudaEvent_t* ev_freq) {
+                      double2* chi, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep) {
   if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "tensor-core contraction not planned");
   TcState& t = *static_cast<TcState*>(c->tc);
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
   const int64_t n2 = (int64_t)ng * ng;
   // B = rho (frequency independent)
+  PrepOut ob{};
+  ob.hi[0] = (__nv_bfloat16*)t.bh.p;
+  ob.lo[0] = (__nv_bfloat16*)t.bl.p;
   stage_begin(c, CHI0_STAGE_WEIGHTS);
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, nullptr, nt, ng, t.mpad,
-                                   (__nv_bfloat16*)t.bh.p, (__nv_bfloat16*)t.bl.p);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, nullptr, 1, nt, ng, t.mpad, ob);
   stage_end(c, CHI0_STAGE_WEIGHTS, 1);
-  for (int iw = 0; iw < nw; ++iw) {
-    stage_begin(c, CHI0_STAGE_WEIGHTS);
-    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, w + (size_t)iw * nt, nt, ng, t.mpad,
-                                     (__nv_bfloat16*)t.ah.p, (__nv_bfloat16*)t.al.p);
-    stage_end(c, CHI0_STAGE_WEIGHTS, 1);
-    stage_begin(c, CHI0_STAGE_CONTRACT);
-    k_herk_bf16x3<<<dim3(t.ntiles, t.nchunks), kThreads, kSmemBytes, c->st>>>(
-        t.m_ah, t.m_al, t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
-        (int*)c->d_err.p);
-    stage_end(c, CHI0_STAGE_CONTRACT, 1);
-    stage_begin(c, CHI0_STAGE_REDUCE);
-    k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
-        (const double2*)t.part.p, t.nchunks, t.ntiles, ng, chi + (size_t)iw * n2);
-    stage_end(c, CHI0_STAGE_REDUCE, 1);
-    if (ev_freq) cudaEventRecord(ev_freq[iw], c->st);
+  PrepOut oa{};
+  for (int g = 0; g < t.group; ++g) {
+    oa.hi[g] = (__nv_bfloat16*)t.ah[g].p;
+    oa.lo[g] = (__nv_bfloat16*)t.al[g].p;
   }
-  // operand split: R read, hi/lo written (B once, A per frequency)
-  c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(nw + 1) * ((double)nt * ng * 8 + 4.0 * t.mpad * t.kpad);
+  const int nunits = t.ntiles * t.nchunks;
+  const unsigned hgrid = (unsigned)std::min(nunits, std::max(1, t.nsm));
+  int passes = 0;
+  for (int w0 = 0; w0 < nw; w0 += t.group, ++passes) {
+    const int gw = std::min(t.group, nw - w0);
+    stage_begin(c, CHI0_STAGE_WEIGHTS);
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, w + (size_t)w0 * nt, gw, nt, ng, t.mpad, oa);
+    stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+    if (ev_prep)
+      for (int g = 0; g < gw; ++g) cudaEventRecord(ev_prep[w0 + g], c->st);
+    for (int g = 0; g < gw; ++g) {
+      const int iw = w0 + g;
+      stage_begin(c, CHI0_STAGE_CONTRACT);
+      k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
+          t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
+          nunits, (int*)c->d_err.p);
+      stage_end(c, CHI0_STAGE_CONTRACT, 1);
+      stage_begin(c, CHI0_STAGE_REDUCE);
+      k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
+          (const double2*)t.part.p, t.nchunks, t.ntiles, ng, chi + (size_t)iw * n2);
+      stage_end(c, CHI0_STAGE_REDUCE, 1);
+      if (ev_freq) cudaEventRecord(ev_freq[iw], c->st);
+    }
+  }
+  // operand split: R read once per pass, hi/lo written (B once, A per frequency)
+  c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(passes + 1) * nt * ng * 8 + (double)(nw + 1) * 4.0 * t.mpad * t.kpad;
   // contraction: each launch streams A and B (hi and lo) once and writes its chunk partials
   c->stage[CHI0_STAGE_CONTRACT].bytes =
       (double)nw * (8.0 * t.mpad * t.kpad + (double)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16);
@@ -576,9 +650,13 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
 void tc_release(chi0_ctx* c) {
   if (!c->tc) return;
   TcState* t = static_cast<TcState*>(c->tc);
-  DevBuf* bufs[] = {&t->ah, &t->al, &t->bh, &t->bl, &t->part};
+  DevBuf* bufs[] = {&t->bh, &t->bl, &t->part};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  for (int g = 0; g < kPrepGroup; ++g) {
+    if (t->ah[g].p) cudaFree(t->ah[g].p);
+    if (t->al[g].p) cudaFree(t->al[g].p);
+  }
   delete t;
   c->tc = nullptr;
 }
