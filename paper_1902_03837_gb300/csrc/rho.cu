@@ -247,6 +247,13 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
   const int nyb = (HY + kHYT - 1) / kHYT;
   const int nzb = (HZ + kHZY - 1) / kHZY;
   const int yhalf = (N2 + 1) / 2;
+  // radix-4 stage Y when N2 is a multiple of 4: Q4 = N2 / 4 points per
+  // residue; the hy of one class mod 4 are ceil(HY / 4) at most, taken kHYT
+  // at a time (ncc chunks)
+  const bool radix4 = (N2 % 4) == 0;
+  const int Q4 = N2 / 4;
+  const int qhalf = (Q4 + 1) / 2;
+  const int ncc = ((HY + 3) / 4 + kHYT - 1) / kHYT;
   __syncthreads();
 
   // plane loads: the n band into the padded rows, the m bands, and the
@@ -314,47 +321,117 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
     }
     __syncthreads();
 
-    // ---- stage Y: ys[half][j][hy][hz] = sum_{y in half} e^{2 pi i hy y / N2} zs[j][hz][y]
-    for (int it = tid; it < 2 * cm * nyb * nzb; it += kRhoThreads) {
-      const int half = it / (cm * nyb * nzb);
-      const int r0 = it - half * (cm * nyb * nzb);
-      const int j = r0 / (nyb * nzb);
-      const int r = r0 - j * (nyb * nzb);
-      const int zb = r / nyb, yb = r - zb * nyb;
-      T2 a[kHYT][kHZY];
+    if (radix4) {
+      // ---- stage Y, radix-4 form (N2 = 4 Q): with y = Q s + r,
+      //   Y(hy) = sum_r e^{2 pi i hy r / N2} W_c(r),  W_c(r) = sum_s i^{c s} z(Q s + r),
+      // c = hy mod 4.  Y1 replaces each zs row by W_0..W_3 (butterflies, no
+      // multiplies); Y2 takes the hy of one residue class together, so that
+      // they share the W_c loads, over half of the r range per work item.
+      for (int it = tid; it < cm * HZ * Q4; it += kRhoThreads) {
+        const int r = it % Q4, row = it / Q4;
+        T2* zr = zs + (size_t)row * N2P;
+        const T2 z0 = zr[r], z1 = zr[Q4 + r], z2 = zr[2 * Q4 + r], z3 = zr[3 * Q4 + r];
+        T2 w;
+        w.x = (z0.x + z2.x) + (z1.x + z3.x);  // c = 0
+        w.y = (z0.y + z2.y) + (z1.y + z3.y);
+        zr[r] = w;
+        w.x = (z0.x - z2.x) - (z1.y - z3.y);  // c = 1: z0 + i z1 - z2 - i z3
+        w.y = (z0.y - z2.y) + (z1.x - z3.x);
+        zr[Q4 + r] = w;
+        w.x = (z0.x + z2.x) - (z1.x + z3.x);  // c = 2
+        w.y = (z0.y + z2.y) - (z1.y + z3.y);
+        zr[2 * Q4 + r] = w;
+        w.x = (z0.x - z2.x) + (z1.y - z3.y);  // c = 3: z0 - i z1 - z2 + i z3
+        w.y = (z0.y - z2.y) - (z1.x - z3.x);
+        zr[3 * Q4 + r] = w;
+      }
+      __syncthreads();
+      const int nit = 2 * cm * 4 * ncc * nzb;
+      for (int it = tid; it < nit; it += kRhoThreads) {
+        int r0 = it;
+        const int zb = r0 % nzb; r0 /= nzb;
+        const int mc = r0 % ncc; r0 /= ncc;
+        const int c = r0 % 4; r0 /= 4;
+        const int j = r0 % cm;
+        const int half = r0 / cm;
+        const int c0 = pmod(c - hy_base, 4);  // first hy_rel of the class
+        T2 a[kHYT][kHZY];
 #pragma unroll
-      for (int h = 0; h < kHYT; ++h)
+        for (int h = 0; h < kHYT; ++h)
 #pragma unroll
-        for (int z = 0; z < kHZY; ++z) a[h][z] = czero<T2>();
-      const int hz0 = min(zb * kHZY, HZ - 1);
-      const int hz1 = min(zb * kHZY + 1, HZ - 1);
-      const T2* z0p = zs + ((size_t)j * HZ + hz0) * N2P;
-      const T2* z1p = zs + ((size_t)j * HZ + hz1) * N2P;
-      const int hy0 = yb * kHYT;
-      const int ylo = half * yhalf, yhi = min(N2, ylo + yhalf);
-      const T2* tp[kHYT];
+          for (int z = 0; z < kHZY; ++z) a[h][z] = czero<T2>();
+        const int hz0 = min(zb * kHZY, HZ - 1);
+        const int hz1 = min(zb * kHZY + 1, HZ - 1);
+        const T2* w0p = zs + ((size_t)j * HZ + hz0) * N2P + c * Q4;
+        const T2* w1p = zs + ((size_t)j * HZ + hz1) * N2P + c * Q4;
+        const T2* tp[kHYT];
 #pragma unroll
-      for (int h = 0; h < kHYT; ++h) tp[h] = twy + (size_t)min(hy0 + h, HY - 1) * N2P;
-      for (int y = ylo; y < yhi; ++y) {
-        const T2 v0 = z0p[y], v1 = z1p[y];
+        for (int h = 0; h < kHYT; ++h)
+          tp[h] = twy + (size_t)min(c0 + 4 * (mc * kHYT + h), HY - 1) * N2P;
+        const int rlo = half * qhalf, rhi = min(Q4, rlo + qhalf);
+        for (int r = rlo; r < rhi; ++r) {
+          const T2 v0 = w0p[r], v1 = w1p[r];
+#pragma unroll
+          for (int h = 0; h < kHYT; ++h) {
+            const T2 t = tp[h][r];
+            cmac(a[h][0], t, v0);
+            cmac(a[h][1], t, v1);
+          }
+        }
+        T2* yo = ys + (size_t)half * JM * HY * HZ;
 #pragma unroll
         for (int h = 0; h < kHYT; ++h) {
-          const T2 t = tp[h][y];
-          cmac(a[h][0], t, v0);
-          cmac(a[h][1], t, v1);
+          const int hyr = c0 + 4 * (mc * kHYT + h);
+          if (hyr < HY) {
+            yo[((size_t)j * HY + hyr) * HZ + hz0] = a[h][0];
+            if (zb * kHZY + 1 < HZ) yo[((size_t)j * HY + hyr) * HZ + hz1] = a[h][1];
+          }
         }
       }
-      T2* yo = ys + (size_t)half * JM * HY * HZ;
-#pragma unroll
-      for (int h = 0; h < kHYT; ++h) {
-        const int hyr = hy0 + h;
-        if (hyr < HY) {
-          yo[((size_t)j * HY + hyr) * HZ + hz0] = a[h][0];
-          if (zb * kHZY + 1 < HZ) yo[((size_t)j * HY + hyr) * HZ + hz1] = a[h][1];
+      __syncthreads();
+    } else {
+      // ---- stage Y: ys[half][j][hy][hz] = sum_{y in half} e^{2 pi i hy y / N2} zs[j][hz][y]
+      for (int it = tid; it < 2 * cm * nyb * nzb; it += kRhoThreads) {
+        const int half = it / (cm * nyb * nzb);
+        const int r0 = it - half * (cm * nyb * nzb);
+        const int j = r0 / (nyb * nzb);
+        const int r = r0 - j * (nyb * nzb);
+        const int zb = r / nyb, yb = r - zb * nyb;
+        T2 a[kHYT][kHZY];
+  #pragma unroll
+        for (int h = 0; h < kHYT; ++h)
+  #pragma unroll
+          for (int z = 0; z < kHZY; ++z) a[h][z] = czero<T2>();
+        const int hz0 = min(zb * kHZY, HZ - 1);
+        const int hz1 = min(zb * kHZY + 1, HZ - 1);
+        const T2* z0p = zs + ((size_t)j * HZ + hz0) * N2P;
+        const T2* z1p = zs + ((size_t)j * HZ + hz1) * N2P;
+        const int hy0 = yb * kHYT;
+        const int ylo = half * yhalf, yhi = min(N2, ylo + yhalf);
+        const T2* tp[kHYT];
+  #pragma unroll
+        for (int h = 0; h < kHYT; ++h) tp[h] = twy + (size_t)min(hy0 + h, HY - 1) * N2P;
+        for (int y = ylo; y < yhi; ++y) {
+          const T2 v0 = z0p[y], v1 = z1p[y];
+  #pragma unroll
+          for (int h = 0; h < kHYT; ++h) {
+            const T2 t = tp[h][y];
+            cmac(a[h][0], t, v0);
+            cmac(a[h][1], t, v1);
+          }
+        }
+        T2* yo = ys + (size_t)half * JM * HY * HZ;
+  #pragma unroll
+        for (int h = 0; h < kHYT; ++h) {
+          const int hyr = hy0 + h;
+          if (hyr < HY) {
+            yo[((size_t)j * HY + hyr) * HZ + hz0] = a[h][0];
+            if (zb * kHZY + 1 < HZ) yo[((size_t)j * HY + hyr) * HZ + hz1] = a[h][1];
+          }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
 
     // the planes of x are no longer read: start copying those of x + 1
     if (x + 1 < g.N1) issue_plane(x + 1);
@@ -390,7 +467,7 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
 }
 
 template <typename T, int JM, typename TOUT>
-__global__ void __launch_bounds__(kRhoThreads) k_rho_pairs(const RhoTask<T, TOUT> tk) {
+__global__ void __launch_bounds__(kRhoThreads, sizeof(T) == 4 ? 2 : 1) k_rho_pairs(const RhoTask<T, TOUT> tk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   rho_block<T, JM, TOUT>(tk, blockIdx.x, smem_raw);
 }
@@ -400,7 +477,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_pairs(const RhoTask<T, TOUT
 // problems (systems / q points) with their own geometry; task i owns global
 // blocks [block0_i, block0_{i+1}).
 template <typename T, int JM, typename TOUT>
-__global__ void __launch_bounds__(kRhoThreads)
+__global__ void __launch_bounds__(kRhoThreads, sizeof(T) == 4 ? 2 : 1)
 k_rho_batch(const RhoTask<T, TOUT>* __restrict__ tasks, int ntasks, int64_t total,
             unsigned long long* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
