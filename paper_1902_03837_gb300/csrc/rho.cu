@@ -285,16 +285,40 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       const T2* pn = unp + (size_t)(sm.padz + hz_base + hb * kHZT) * N2 + y;
       const T2* pm = ums + y;
       if (cm == JM) {
-        for (int b = 0; b < NZ; ++b, pn += N2, pm += N2) {
-          T2 um[JM], un[kHZT];
+        // U_n rows hz .. hz + kHZT - 1 at b slide by one row per b: keep the
+        // window in registers (three names, rotated by unrolling) and load
+        // one new row per b
+        static_assert(kHZT == 3, "the rotation below is written for three rows");
+        T2 w0 = pn[0], w1 = pn[N2], w2;
+        const T2* pl = pn + 2 * N2;  // next row of U_n to load
+        int b = 0;
+        auto step = [&](const T2 r0, const T2 r1, const T2 r2) {
+          T2 um[JM];
 #pragma unroll
           for (int j = 0; j < JM; ++j) um[j] = pm[j * (int)plane];
 #pragma unroll
-          for (int h = 0; h < kHZT; ++h) un[h] = pn[h * N2];
-#pragma unroll
-          for (int j = 0; j < JM; ++j)
-#pragma unroll
-            for (int h = 0; h < kHZT; ++h) cjmac(a[j][h], un[h], um[j]);
+          for (int j = 0; j < JM; ++j) {
+            cjmac(a[j][0], r0, um[j]);
+            cjmac(a[j][1], r1, um[j]);
+            cjmac(a[j][2], r2, um[j]);
+          }
+          pm += N2;
+        };
+        for (; b + 3 <= NZ; b += 3) {
+          w2 = pl[0];
+          step(w0, w1, w2);
+          w0 = pl[N2];
+          step(w1, w2, w0);
+          w1 = pl[2 * N2];
+          step(w2, w0, w1);
+          pl += 3 * N2;
+        }
+        for (; b < NZ; ++b) {
+          w2 = pl[0];
+          step(w0, w1, w2);
+          w0 = w1;
+          w1 = w2;
+          pl += N2;
         }
       } else {
         for (int b = 0; b < NZ; ++b, pn += N2, pm += N2) {
@@ -348,12 +372,14 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       __syncthreads();
       const int nit = 2 * cm * 4 * ncc * nzb;
       for (int it = tid; it < nit; it += kRhoThreads) {
+        // j fastest, then the residue class: the 16 threads of a half-warp
+        // read rows at offsets 13 j + 12 c (mod 16 words), all distinct
         int r0 = it;
-        const int zb = r0 % nzb; r0 /= nzb;
-        const int mc = r0 % ncc; r0 /= ncc;
+        const int j = r0 % cm; r0 /= cm;
         const int c = r0 % 4; r0 /= 4;
-        const int j = r0 % cm;
-        const int half = r0 / cm;
+        const int zb = r0 % nzb; r0 /= nzb;
+        const int mc = r0 % ncc;
+        const int half = r0 / ncc;
         const int c0 = pmod(c - hy_base, 4);  // first hy_rel of the class
         T2 a[kHYT][kHZY];
 #pragma unroll
