@@ -43,6 +43,24 @@ def chi0_flops(ng, nt, nw):
     return 4.0 * ng * (ng + 1) * nt * nw
 
 
+# stage -> (binding roof, unit, kernel)
+STAGE_ROOF = {"contract": ("tensor", "TFLOP/s", "k_herk_bf16x3"), "rho": ("alu", "TFLOP/s", "k_rho_pairs"),
+              "wf_grid": ("alu", "TFLOP/s", "k_wf_to_mixed"), "dyson": ("fp64", "TFLOP/s", "k_gj_update"),
+              "weights": ("hbm", "GB/s", "k_prep"), "reduce": ("hbm", "GB/s", "k_tc_reduce")}
+# FP32 FMA: 152 SMs x 128 lanes x 2 flop x 1.93 GHz (the clock seen under this load)
+FP32_PEAK, FP32_SRC = 75.0, "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 1.93 GHz"
+# FP64: the nominal GB300 figure (no measured FP64 peak is available)
+FP64_PEAK, FP64_SRC = 1.25, "FP64 nominal (GB300)"
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel on
+# this workload (one-pass dram__bytes_read.sum + dram__bytes_write.sum at full
+# size); to be removed once the kernel changes after the capture.
+TRAFFIC = {
+    ("k_herk_bf16x3", WORKLOAD): (5.31e10, "ncu, mean of 4 full-size launches (one frequency each)"),
+    ("k_rho_pairs", WORKLOAD): (4.42e10, "ncu, one full-size launch"),
+    ("k_prep", WORKLOAD): (6.60e10, "ncu, one full-size four-frequency pass"),
+}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -180,7 +198,8 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.current_stream(dev)
     s = build_system(args.kgrid, args.nw)
     ng, nw = s.ng, s.freqs.size
-    ctx = lib.Chi0.for_system(s, precision=lib.CHI0_MIXED_BF16X3, stream=stream.cuda_stream)
+    prec = lib.CHI0_MIXED_BF16X3 if args.precision == "mixed" else lib.CHI0_FP64
+    ctx = lib.Chi0.for_system(s, precision=prec, stream=stream.cuda_stream)
     # inputs resident in HBM (device-to-device set keeps the timed region free of host copies)
     gv_d = [torch.from_numpy(np.ascontiguousarray(s.gvec[ik, :s.npw[ik]])).to(dev) for ik in range(s.nk)]
     cf_d = [torch.from_numpy(np.ascontiguousarray(s.coef[ik, :, :s.npw[ik]])).to(dev) for ik in range(s.nk)]
@@ -241,53 +260,77 @@ def run_ours(args, rank, world, dist):
         ctx.compute_rho(0)
         ctx.build_invert(0, out_h)   # device -> host copy of the result, synchronises
 
-    e2e_step()
-    e2e_steps = max(1, min(args.steps, 3))
-    barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    if args.no_e2e:
+        e2e_ms = None
+    else:
         e2e_step()
-    torch.cuda.synchronize(dev)
-    barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * flops_step / (e2e_ms * 1e-3) / 1e12
+        e2e_steps = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        if dist is not None:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
     ctx.get_stats()
     ctx.close()
 
     if rank != 0:
         return
     pk = peaks()
-    # dominant kernel: the stage with the largest device time
+    # dominant kernel: the stage with the largest device time (events on the
+    # stream each stage's kernels are launched on)
     dom = max(st_ms, key=lambda k: st_ms[k])
     per_step_ms = {k: v / args.steps for k, v in st_ms.items()}
-    kinds = {"contract": ("tensor", "TFLOP/s"), "rho": ("alu", "TFLOP/s"), "wf_grid": ("alu", "TFLOP/s"),
-             "dyson": ("alu", "TFLOP/s"), "weights": ("hbm", "GB/s"), "reduce": ("hbm", "GB/s")}
-    bound, unit = kinds[dom]
+    roofs = dict(STAGE_ROOF)
+    if args.precision == "fp64":  # every stage on the FP64 units
+        roofs.update({"contract": ("fp64", "TFLOP/s", "k_chi0_fp64"), "rho": ("fp64", "TFLOP/s", "k_rho_pairs"),
+                      "wf_grid": ("fp64", "TFLOP/s", "k_wf_to_mixed")})
+    bound, unit, kname = roofs[dom]
+    extra = {}
     if unit == "GB/s":
         achieved = st_bytes[dom] / (per_step_ms[dom] * 1e-3) / 1e9
         peak, psrc = pk["hbm_gbs"], f"HBM copy ({pk['source']})"
     elif bound == "tensor":
+        # algorithmic Hermitian count (4 N_G (N_G + 1) N_T per frequency) over
+        # the contraction time; beside it the tensor pipe's share of the BF16
+        # products actually issued (3 per k-step over the lower-triangle tiles)
         achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
         peak, psrc = pk["bf16_tflops_sustained"], f"BF16 dense sustained ({pk['source']})"
+        mpad = -(-2 * ng // 128) * 128
+        kpad = -(-nt // 64) * 64
+        nT = mpad // 128
+        issued = 3 * 2 * 128 * 128 * (nT * (nT + 1) // 2) * kpad * nw
+        extra = {"issued_tflops": issued / (per_step_ms[dom] * 1e-3) / 1e12,
+                 "issued_frac": issued / (per_step_ms[dom] * 1e-3) / 1e12 / peak}
+    elif bound == "fp64":
+        achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
+        peak, psrc = FP64_PEAK, FP64_SRC
     else:
         achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
-        peak, psrc = 75.0, "FP32 FMA 152 SMs x 128 lanes x 2 x ~1.93 GHz (probe-measured 75.0)"
+        peak, psrc = FP32_PEAK, FP32_SRC
+    traffic, tsrc = TRAFFIC.get((kname, workload_name(args)), (None, None)) if args.precision == "mixed" else (None, None)
+    roof = {"kernel": kname, "stage": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "peak_source": psrc, "traffic": traffic}
+    if tsrc:
+        roof["traffic_source"] = tsrc
+    roof.update(extra)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)", "data": "synthetic",
+        "vs_baseline": None, "dtype": ("bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)" if args.precision == "mixed" else "f64"), "data": "synthetic",
         "config": {"workload": workload_name(args), "n_transitions": nt, "l2": "inputs larger than L2 (mixed grids 32 GB, rho 12 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "stage_ms_per_step": per_step_ms,
-        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "peak_source": psrc, "traffic": None},
-        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "e2e": (None if e2e_ms is None else
+                {"value": world * flops_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -313,6 +356,10 @@ def main():
     ap.add_argument("--kgrid", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     help="smaller k grid for profiling runs, e.g. 4,2,2 (default 8,8,8)")
     ap.add_argument("--nw", type=int, default=32, help="number of imaginary frequencies")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="mixed: FP32 rho, BF16x3 tensor-core chi0, FP64 Dyson (default); "
+                         "fp64: the plain FP64 form of every step, for the speedup comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

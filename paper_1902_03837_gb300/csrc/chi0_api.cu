@@ -326,13 +326,16 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
     a1.flops = 8.0 * (double)c->nk * c->nb * g.NZ *
                ((double)g.NX * g.N2 * g.NY + (double)g.N1 * g.N2 * g.NX);
     // rho: every transition reads two N1 x NZ x N2 mixed grids and writes ng values;
-    // executed complex multiply-adds per transition and x plane: the z
-    // correlation (N2 HZ NZ), the pruned y transform (HY HZ N2), the x
-    // accumulation (ng)
+    // executed work per transition and x plane: the z correlation (N2 HZ NZ
+    // complex multiply-adds), the pruned y transform (HY HZ N2 / 4 multiply-adds
+    // plus 6 HZ N2 flops of radix-4 butterflies when N2 % 4 == 0, else HY HZ N2
+    // multiply-adds), the x accumulation (ng multiply-adds)
     auto& a2 = c->stage[CHI0_STAGE_RHO];
     a2.bytes = (double)c->nt * g.ng * cb + (double)ubytes;
-    a2.flops = 8.0 * (double)c->nt * g.N1 *
-               ((double)g.N2 * g.HZ * g.NZ + (double)g.HY * g.HZ * g.N2 + (double)g.ng);
+    const double ywork = (g.N2 % 4 == 0) ? 8.0 * g.HY * g.HZ * (g.N2 / 4) + 6.0 * g.HZ * g.N2
+                                         : 8.0 * g.HY * g.HZ * g.N2;
+    a2.flops = (double)c->nt * g.N1 *
+               (8.0 * g.N2 * g.HZ * g.NZ + ywork + 8.0 * g.ng);
   }
   return CHI0_OK;
 }
