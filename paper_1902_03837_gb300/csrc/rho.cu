@@ -111,6 +111,91 @@ k_wf_to_mixed(RhoGeom g, const int32_t* __restrict__ gvec, const int32_t* __rest
   }
   __syncthreads();
   T2* out = U + ((size_t)ik * g.nb + band) * ((size_t)g.N1 * g.NZ * g.N2);
+  if (g.N1 % 4 == 0 && g.N2 % 4 == 0) {
+    // Radix-4 on the output side: with N = 4 Q and x = x0 + Q x1,
+    //   u(x0 + Q x1) = sum_c i^{c x1} S_c(x0),  S_c(x0) = sum_{g = c mod 4} a(g) e^{2 pi i g x0 / N},
+    // so each work item takes one x0 (all inputs once, into four partial
+    // sums) and writes four outputs.
+    const int Q1 = g.N1 / 4, Q2 = g.N2 / 4;
+    // P[k] sums the inputs of index = k mod 4; their frequency class is
+    // (c0 + k) mod 4, c0 = the class of index 0
+    auto by_class = [](const T2 (&P)[4], int c0, T2 (&S)[4]) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = (c - c0) & 3;
+        S[c] = k == 0 ? P[0] : k == 1 ? P[1] : k == 2 ? P[2] : P[3];
+      }
+    };
+    auto emit4 = [](const T2 (&S)[4], T2 (&o)[4]) {
+      o[0].x = (S[0].x + S[2].x) + (S[1].x + S[3].x);  // x1 = 0
+      o[0].y = (S[0].y + S[2].y) + (S[1].y + S[3].y);
+      o[1].x = (S[0].x - S[2].x) - (S[1].y - S[3].y);  // x1 = 1: S0 + i S1 - S2 - i S3
+      o[1].y = (S[0].y - S[2].y) + (S[1].x - S[3].x);
+      o[2].x = (S[0].x + S[2].x) - (S[1].x + S[3].x);  // x1 = 2
+      o[2].y = (S[0].y + S[2].y) - (S[1].y + S[3].y);
+      o[3].x = (S[0].x - S[2].x) + (S[1].y - S[3].y);  // x1 = 3: S0 - i S1 - S2 + i S3
+      o[3].y = (S[0].y - S[2].y) - (S[1].x - S[3].x);
+    };
+    for (int zz = 0; zz < g.NZ; ++zz) {
+      const T2* bz = box + zz * g.NX * g.NY;
+      for (int it = tid; it < g.NX * Q2; it += nth) {
+        const int gxr = it / Q2, y0 = it - gxr * Q2;
+        int idx = pmod(-g.Ly * y0, g.N2);
+        T2 P[4] = {czero<T2>(), czero<T2>(), czero<T2>(), czero<T2>()};  // by gyr mod 4
+        const T2* brow = bz + gxr * g.NY;
+        int gyr = 0;
+        for (; gyr + 4 <= g.NY; gyr += 4) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            cmac(P[k], brow[gyr + k], tw2[idx]);
+            idx += y0;
+            if (idx >= g.N2) idx -= g.N2;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (gyr + k < g.NY) {
+            cmac(P[k], brow[gyr + k], tw2[idx]);
+            idx += y0;
+            if (idx >= g.N2) idx -= g.N2;
+          }
+        T2 S[4], o[4];
+        by_class(P, pmod(-g.Ly, 4), S);
+        emit4(S, o);
+#pragma unroll
+        for (int y1 = 0; y1 < 4; ++y1) t1[gxr * g.N2 + y0 + Q2 * y1] = o[y1];
+      }
+      __syncthreads();
+      for (int it = tid; it < Q1 * g.N2; it += nth) {
+        const int x0 = it / g.N2, y = it - x0 * g.N2;
+        int idx = pmod(-g.Lx * x0, g.N1);
+        T2 P[4] = {czero<T2>(), czero<T2>(), czero<T2>(), czero<T2>()};  // by gxr mod 4
+        int gxr = 0;
+        for (; gxr + 4 <= g.NX; gxr += 4) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            cmac(P[k], t1[(gxr + k) * g.N2 + y], tw1[idx]);
+            idx += x0;
+            if (idx >= g.N1) idx -= g.N1;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (gxr + k < g.NX) {
+            cmac(P[k], t1[(gxr + k) * g.N2 + y], tw1[idx]);
+            idx += x0;
+            if (idx >= g.N1) idx -= g.N1;
+          }
+        T2 S[4], o[4];
+        by_class(P, pmod(-g.Lx, 4), S);
+        emit4(S, o);
+#pragma unroll
+        for (int x1 = 0; x1 < 4; ++x1) out[((size_t)(x0 + Q1 * x1) * g.NZ + zz) * g.N2 + y] = o[x1];
+      }
+      __syncthreads();
+    }
+    return;
+  }
   for (int zz = 0; zz < g.NZ; ++zz) {
     const T2* bz = box + zz * g.NX * g.NY;
     for (int it = tid; it < g.NX * g.N2; it += nth) {

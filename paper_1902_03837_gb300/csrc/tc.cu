@@ -406,7 +406,7 @@ constexpr int kPI = 32;  // complex G per tile
 
 // Up to kPrepGroup frequencies are split in one pass, so that R is read once
 // for all of them (the split is bound by HBM traffic: R in, hi/lo out).
-constexpr int kPrepGroup = 4;
+constexpr int kPrepGroup = 8;
 struct PrepOut {
   __nv_bfloat16* hi[kPrepGroup];
   __nv_bfloat16* lo[kPrepGroup];
