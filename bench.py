@@ -57,7 +57,6 @@ FP64_PEAK, FP64_SRC = 1.25, "FP64 nominal (GB300)"
 TRAFFIC = {
     ("k_herk_bf16x3", WORKLOAD): (5.31e10, "ncu, mean of 4 full-size launches (one frequency each)"),
     ("k_rho_pairs", WORKLOAD): (4.42e10, "ncu, one full-size launch"),
-    ("k_prep", WORKLOAD): (6.60e10, "ncu, one full-size four-frequency pass"),
 }
 
 
