@@ -342,7 +342,7 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
   __syncthreads();
 
   // plane loads: the n band into the padded rows, the m bands, and the
-  // x twiddles; issued asynchronously (the next plane's copies overlap stage X)
+  // x twiddles; issued asynchronously (the next plane's copies overlap stages Y and X)
   auto issue_plane = [&](int x) {
     async_copy(unp + (size_t)sm.padz * N2, Un + (size_t)x * plane, (int)(plane * sizeof(T2)), tid,
                kRhoThreads);
@@ -429,6 +429,10 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       }
     }
     __syncthreads();
+
+    // the planes of x are no longer read (stages Y and X use zs, ys and the
+    // twiddles): start copying those of x + 1, hidden behind stages Y and X
+    if (x + 1 < g.N1) issue_plane(x + 1);
 
     if (radix4) {
       // ---- stage Y, radix-4 form (N2 = 4 Q): with y = Q s + r,
@@ -543,9 +547,6 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       }
       __syncthreads();
     }
-
-    // the planes of x are no longer read: start copying those of x + 1
-    if (x + 1 < g.N1) issue_plane(x + 1);
 
     // ---- stage X: rho(G_i) += e^{2 pi i hx x / N1} (ys[0] + ys[1])[j][hy_i][hz_i]
     const T2* ys1 = ys + (size_t)JM * HY * HZ;
