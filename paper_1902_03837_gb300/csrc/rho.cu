@@ -351,6 +351,21 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
                  (int)(plane * sizeof(T2)), tid, kRhoThreads);
   };
   issue_plane(0);
+  // This thread's first work item of stages Z, Y1 and Y2 is the same for
+  // every x plane: decode it once (packed), so that the plane loop divides
+  // only for later rounds.
+  const int zpack = (tid / N2) << 16 | (tid % N2);                 // stage Z: hb, y
+  const int y1pack = radix4 ? ((tid / Q4) << 16 | (tid % Q4)) : 0;  // stage Y1: row, r
+  int y2pack = 0;                                                   // stage Y2 (bit fields)
+  if (radix4) {
+    int r0 = tid;
+    const int j = r0 % cm; r0 /= cm;
+    const int c = r0 % 4; r0 /= 4;
+    const int zb = r0 % nzb; r0 /= nzb;
+    const int mc = r0 % ncc;
+    const int half = r0 / ncc;
+    y2pack = j | c << 4 | zb << 8 | mc << 16 | half << 24;
+  }
   cp_async_wait_all();
   __syncthreads();
 
@@ -360,7 +375,8 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
 
     // ---- stage Z: zs[j][hz][y] = sum_b conj(U_n(y, b + hz)) U_m,j(y, b)
     for (int it = tid; it < N2 * nhb; it += kRhoThreads) {
-      const int hb = it / N2, y = it - hb * N2;
+      const int hb = it == tid ? zpack >> 16 : it / N2;
+      const int y = it == tid ? zpack & 0xffff : it - hb * N2;
       T2 a[JM][kHZT];
 #pragma unroll
       for (int j = 0; j < JM; ++j)
@@ -441,7 +457,8 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       // multiplies); Y2 takes the hy of one residue class together, so that
       // they share the W_c loads, over half of the r range per work item.
       for (int it = tid; it < cm * HZ * Q4; it += kRhoThreads) {
-        const int r = it % Q4, row = it / Q4;
+        const int r = it == tid ? y1pack & 0xffff : it % Q4;
+        const int row = it == tid ? y1pack >> 16 : it / Q4;
         T2* zr = zs + (size_t)row * N2P;
         const T2 z0 = zr[r], z1 = zr[Q4 + r], z2 = zr[2 * Q4 + r], z3 = zr[3 * Q4 + r];
         T2 w;
@@ -463,12 +480,21 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       for (int it = tid; it < nit; it += kRhoThreads) {
         // j fastest, then the residue class: the 16 threads of a half-warp
         // read rows at offsets 13 j + 12 c (mod 16 words), all distinct
-        int r0 = it;
-        const int j = r0 % cm; r0 /= cm;
-        const int c = r0 % 4; r0 /= 4;
-        const int zb = r0 % nzb; r0 /= nzb;
-        const int mc = r0 % ncc;
-        const int half = r0 / ncc;
+        int j, c, zb, mc, half;
+        if (it == tid) {
+          j = y2pack & 15;
+          c = (y2pack >> 4) & 15;
+          zb = (y2pack >> 8) & 255;
+          mc = (y2pack >> 16) & 255;
+          half = y2pack >> 24;
+        } else {
+          int r0 = it;
+          j = r0 % cm; r0 /= cm;
+          c = r0 % 4; r0 /= 4;
+          zb = r0 % nzb; r0 /= nzb;
+          mc = r0 % ncc;
+          half = r0 / ncc;
+        }
         const int c0 = pmod(c - hy_base, 4);  // first hy_rel of the class
         T2 a[kHYT][kHZY];
 #pragma unroll
