@@ -43,6 +43,30 @@ __device__ __forceinline__ void cjmac(T2& acc, const T2 a, const T2 b) {  // acc
   acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// Stage Z step conj(a) b with packed FP32 arithmetic: per component the same
+// fused multiply-adds as cjmac, in the same order, issued two at a time:
+//   acc += (a.x, a.x) * (b.x, b.y),  acc += (a.y, a.y) * (b.y, -b.x).
+// A U_n value enters the z window once as (a.x, a.x), (a.y, a.y); the FP64
+// kernel keeps the scalar form.
+template <typename T2> struct ZRow { T2 v; };
+template <> struct ZRow<float2> { float2 xx, yy; };
+__device__ __forceinline__ ZRow<float2> zrow(const float2 a) {
+  ZRow<float2> r;
+  r.xx = make_float2(a.x, a.x);
+  r.yy = make_float2(a.y, a.y);
+  return r;
+}
+__device__ __forceinline__ ZRow<double2> zrow(const double2 a) { return ZRow<double2>{a}; }
+__device__ __forceinline__ float2 zrot(const float2 b) { return make_float2(b.y, -b.x); }
+__device__ __forceinline__ double2 zrot(const double2 b) { return b; }
+__device__ __forceinline__ void zmac(float2& acc, const ZRow<float2>& a, const float2 b, const float2 rb) {
+  acc = __ffma2_rn(a.xx, b, acc);
+  acc = __ffma2_rn(a.yy, rb, acc);
+}
+__device__ __forceinline__ void zmac(double2& acc, const ZRow<double2>& a, const double2 b, const double2) {
+  cjmac(acc, a.v, b);
+}
+
 template <typename T2>
 __device__ __forceinline__ T2 czero() {
   T2 z;
@@ -390,32 +414,31 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
         // window in registers (three names, rotated by unrolling) and load
         // one new row per b
         static_assert(kHZT == 3, "the rotation below is written for three rows");
-        T2 w0 = pn[0], w1 = pn[N2], w2;
+        ZRow<T2> w0 = zrow(pn[0]), w1 = zrow(pn[N2]), w2;
         const T2* pl = pn + 2 * N2;  // next row of U_n to load
         int b = 0;
-        auto step = [&](const T2 r0, const T2 r1, const T2 r2) {
-          T2 um[JM];
-#pragma unroll
-          for (int j = 0; j < JM; ++j) um[j] = pm[j * (int)plane];
+        auto step = [&](const ZRow<T2>& r0, const ZRow<T2>& r1, const ZRow<T2>& r2) {
 #pragma unroll
           for (int j = 0; j < JM; ++j) {
-            cjmac(a[j][0], r0, um[j]);
-            cjmac(a[j][1], r1, um[j]);
-            cjmac(a[j][2], r2, um[j]);
+            const T2 um = pm[j * (int)plane];
+            const T2 rm = zrot(um);
+            zmac(a[j][0], r0, um, rm);
+            zmac(a[j][1], r1, um, rm);
+            zmac(a[j][2], r2, um, rm);
           }
           pm += N2;
         };
         for (; b + 3 <= NZ; b += 3) {
-          w2 = pl[0];
+          w2 = zrow(pl[0]);
           step(w0, w1, w2);
-          w0 = pl[N2];
+          w0 = zrow(pl[N2]);
           step(w1, w2, w0);
-          w1 = pl[2 * N2];
+          w1 = zrow(pl[2 * N2]);
           step(w2, w0, w1);
           pl += 3 * N2;
         }
         for (; b < NZ; ++b) {
-          w2 = pl[0];
+          w2 = zrow(pl[0]);
           step(w0, w1, w2);
           w0 = w1;
           w1 = w2;
