@@ -16,7 +16,9 @@ theory calculations using the yambo code", J. Phys.: Condens. Matter 31,
 * the Dyson step by Gauss-Jordan elimination with partial pivoting, and
   independently by the linear solve of Eq. (X_rpa_inv);
 * the bare Coulomb interaction v(q+G) = 4 pi / |q+G|^2 of the Coulomb
-  interaction subsection and the symmetric form of Eq. (W_def).
+  interaction subsection and the symmetric form of Eq. (W_def);
+* the Bruneval-Gonze extrapolar correction of Eq. (X_term_def) and
+  Appendix C through the closure relation over the bands at k.
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 against invariants, closed forms or independent routes.
@@ -31,3 +33,4 @@ from .chi0 import (  # noqa: F401
     chi0_lindhard_plane_waves,
 )
 from .dyson import eps_tilde, eps_inv_gauss_jordan, eps_inv_rpa_route  # noqa: F401
+from .bg_terminator import diag_density, extrapolar_weights, delta_chi_bg, chi0_bg  # noqa: F401
