@@ -130,6 +130,13 @@ def build_system(kgrid=None, nw=32):
 
 
 def workload_name(args):
+    base = _workload_base(args)
+    if getattr(args, "bg_terminator", None) is not None:
+        base += f", Bruneval-Gonze extrapolar correction at {args.bg_terminator:g} eV"
+    return base
+
+
+def _workload_base(args):
     if args.kgrid is None and args.nw == 32:
         return WORKLOAD
     k = "x".join(str(v) for v in (args.kgrid or (8, 8, 8)))
@@ -206,6 +213,9 @@ def run_ours(args, rank, world, dist):
     for ik in range(s.nk):
         ctx.set_wavefunctions(ik, gv_d[ik], cf_d[ik])
     ctx.set_energies(s.eps, s.occ)
+    if args.bg_terminator is not None:
+        from synth import HA_EV
+        ctx.set_bg_terminator(args.bg_terminator / HA_EV)
     inv_d = torch.empty((nw, ng, ng), dtype=torch.complex128, device=dev)
 
     def step():
@@ -360,6 +370,8 @@ def main():
                     help="mixed: FP32 rho, BF16x3 tensor-core chi0, FP64 Dyson (default); "
                          "fp64: the plain FP64 form of every step, for the speedup comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--bg-terminator", type=float, default=None, metavar="EV",
+                    help="apply the Bruneval-Gonze extrapolar correction with this extrapolar energy (eV)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

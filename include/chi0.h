@@ -311,6 +311,24 @@ chi0_status chi0_term_features(chi0_ctx* ctx, int iq, const void* chi_trunc, con
  * to correct every following chi0_build_chi0 on ctx; NULL switches it off. */
 chi0_status chi0_set_terminator(chi0_ctx* ctx, const float* params, int bf16);
 
+/* ---- Bruneval-Gonze extrapolar correction (X-terminator) --------------------
+ * Eq. (X_term_def) with Appendix C (Eqs. rhotw-term, F-term, X-term): the
+ * bands that the sum leaves out (band index >= nbands) are given one energy
+ * eps_bar (Ha, absolute) and no occupation.  By the closure relation over the
+ * bands at k their contribution is
+ *   sum_{k,m} wbar_m(w) [ <m k-q| e^{i(G-G').r} |m k-q> - sum_{n<nbands} rho_nm(G) conj(rho_nm(G')) ],
+ * wbar_m(w) the frequency factor of a transition from m into a state at
+ * eps_bar, in the form of the other weights.  on = 1 applies it to every
+ * following chi0_build_chi0 / chi0_build_invert / batch run; on = 0 switches
+ * it off.  Either change requires chi0_compute_rho again (the transition
+ * block then covers every band n < nbands at k, occupied ones included).  The
+ * diagonal densities are taken on the difference vectors G - G' of the
+ * response set; the FFT grid must be alias-free for them
+ * (fft[a] > 2 max|G_a| of the spheres + max|G_a - G'_a|), checked at
+ * chi0_build_chi0.  Excludes the learned terminator (chi0_set_terminator).
+ * Errors: CHI0_EINVAL (eps_bar not finite, learned terminator set). */
+chi0_status chi0_set_bg_terminator(chi0_ctx* ctx, int on, double eps_bar);
+
 /* Text of the last error on ctx (static storage inside ctx; never NULL). */
 const char* chi0_last_error(const chi0_ctx* ctx);
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "chi0_build_chi0", "chi0_invert_eps", "chi0_build_invert", "chi0_get_response_gvectors", "chi0_get_transitions",
     "chi0_get_rho", "chi0_get_rho_rows", "chi0_synchronize", "chi0_get_stats", "chi0_last_error", "chi0_destroy",
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
-    "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator",
+    "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator", "chi0_set_bg_terminator",
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
 )
 
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_mlp_predict.argtypes = [P, P, I64, I, P, P]
     lib.chi0_term_features.argtypes = [P, I, P, P, P, P, P]
     lib.chi0_set_terminator.argtypes = [P, P, I]
+    lib.chi0_set_bg_terminator.argtypes = [P, I, D]
     lib.chi0_batch_create.argtypes = [P, P, P, I, I, ctypes.POINTER(P)]
     lib.chi0_batch_run.argtypes = [P, P]
     lib.chi0_batch_rho_width.argtypes = [P]
@@ -352,6 +353,11 @@ class Chi0:
                                             _dev(chi_full) if chi_full is not None else None, _dev(x),
                                             _dev(t) if t is not None else None, ctypes.byref(sc)))
         return sc.value
+
+    def set_bg_terminator(self, eps_bar, on=True):
+        """chi0_set_bg_terminator: the Bruneval-Gonze extrapolar correction with
+        extrapolar energy eps_bar (Ha); call compute_rho afterwards."""
+        self._check(_lib.chi0_set_bg_terminator(self.h, 1 if on else 0, float(eps_bar)))
 
     def set_terminator(self, params, bf16=True):
         self._check(_lib.chi0_set_terminator(self.h, _dev(params) if params is not None else None,

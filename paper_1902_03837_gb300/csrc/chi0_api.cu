@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -215,6 +216,8 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
       if (f > tol) mmax = std::max(mmax, b);
       if (f < 1.0 - tol) nmin = std::min(nmin, b);
     }
+  // the extrapolar correction subtracts every band n < nb at k (closure)
+  if (c->bg_on) nmin = 0;
   c->Nm = mmax + 1;
   c->n_lo = nmin;
   c->Nn = c->nb - nmin;
@@ -380,6 +383,157 @@ chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
   return CHI0_OK;
 }
 
+// ---- Bruneval-Gonze extrapolar correction: planning and launch
+// Difference vectors d = G_i - G_j of the response set, ordered by (y, z, x)
+// (the order the rho kernel visits its G set in), cut into chunks of at most
+// 4096 (the rho kernel's register accumulators at one m band per block).
+chi0_status plan_bg(chi0_ctx* c) {
+  const int ng = c->cfg.ng, nw = c->cfg.nw;
+  const RhoGeom& g = c->geom;
+  auto less_yzx = [](const std::array<int32_t, 3>& A, const std::array<int32_t, 3>& B) {
+    if (A[1] != B[1]) return A[1] < B[1];
+    if (A[2] != B[2]) return A[2] < B[2];
+    return A[0] < B[0];
+  };
+  std::vector<std::array<int32_t, 3>> dv((size_t)ng * ng);
+  for (int i = 0; i < ng; ++i)
+    for (int j = 0; j < ng; ++j)
+      for (int a = 0; a < 3; ++a)
+        dv[(size_t)i * ng + j][a] = c->h_gresp[3 * i + a] - c->h_gresp[3 * j + a];
+  std::vector<std::array<int32_t, 3>> D(dv);
+  std::sort(D.begin(), D.end(), less_yzx);
+  D.erase(std::unique(D.begin(), D.end()), D.end());
+  const int nd = (int)D.size();
+  std::vector<int32_t> didx((size_t)ng * ng);
+  for (size_t e = 0; e < dv.size(); ++e)
+    didx[e] = (int32_t)(std::lower_bound(D.begin(), D.end(), dv[e], less_yzx) - D.begin());
+  // the densities' products must not alias onto the difference set
+  for (int a = 0; a < 3; ++a) {
+    int dmax = 0;
+    for (const auto& d : D) dmax = std::max(dmax, std::abs(d[a]));
+    const int L = a == 0 ? g.Lx : a == 1 ? g.Ly : g.Lz;
+    if (c->cfg.fft[a] <= 2 * L + dmax)
+      return fail(c, CHI0_EINVAL,
+                  "fft[%d] = %d aliases for the extrapolar densities: need > 2*%d + %d", a,
+                  c->cfg.fft[a], L, dmax);
+  }
+  constexpr int kChunk = 4096;
+  const int nch = (nd + kChunk - 1) / kChunk;
+  if (nch > chi0::kBgMaxChunks)
+    return fail(c, CHI0_EUNSUPPORTED, "%d difference vectors: more than %d chunks", nd, chi0::kBgMaxChunks);
+  const int64_t ntd = (int64_t)c->nk * c->Nm;
+  chi0::BgChunks ch{};
+  ch.n = nch;
+  c->bg_geom.assign(nch, g);
+  for (int k = 0; k < nch; ++k) {
+    const int a0 = k * kChunk, a1 = std::min(nd, a0 + kChunk);
+    ch.start[k] = a0;
+    ch.off[k] = ntd * a0;
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    for (int e = a0; e < a1; ++e)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], D[e][a]);
+        hi[a] = std::max(hi[a], D[e][a]);
+      }
+    RhoGeom& gc = c->bg_geom[k];
+    gc.ng = a1 - a0;
+    gc.Mx_lo = lo[0];
+    gc.My_lo = lo[1];
+    gc.Mz_lo = lo[2];
+    gc.HX = hi[0] - lo[0] + 1;
+    gc.HY = hi[1] - lo[1] + 1;
+    gc.HZ = hi[2] - lo[2] + 1;
+    gc.n_lo = 0;
+    gc.Nn = c->Nm;
+    gc.Nm = 1;
+    gc.diag = 1;
+    gc.g0max = 0;
+    gc.g0z_min = 0;
+    gc.g0z_max = 0;
+  }
+  ch.start[nch] = nd;
+  // extrapolar weights wbar[iw][k * Nm + m] (same pole form as the weights kernel)
+  const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
+  const double tol = c->cfg.occ_drop_tol;
+  std::vector<double> wbar((size_t)nw * ntd, 0.0);
+  for (int iw = 0; iw < nw; ++iw) {
+    const double sw = c->om[2 * iw + 1] + c->cfg.eta;
+    for (int ik = 0; ik < c->nk; ++ik)
+      for (int m = 0; m < c->Nm; ++m) {
+        const double f = c->h_occ[(size_t)ik * c->nb + m];
+        if (!(f > tol)) continue;
+        const double dbar = c->h_eps[(size_t)ik * c->nb + m] - c->bg_eps;
+        const double den = dbar * dbar + sw * sw;
+        if (den > 0.0) wbar[(size_t)iw * ntd + (size_t)ik * c->Nm + m] = pref * f * (2.0 * dbar / den);
+      }
+  }
+  std::vector<int32_t> dflat((size_t)nd * 3), ident(std::min(nd, kChunk)), kid(c->nk), zero((size_t)c->nk * 3, 0);
+  for (int e = 0; e < nd; ++e)
+    for (int a = 0; a < 3; ++a) dflat[(size_t)e * 3 + a] = D[e][a];
+  for (size_t e = 0; e < ident.size(); ++e) ident[e] = (int32_t)e;
+  for (int ik = 0; ik < c->nk; ++ik) kid[ik] = ik;
+  chi0_status s;
+  const size_t cb = cplx_bytes(c);
+  if ((s = ensure(c, c->d_bgd, dflat.size() * 4, "difference vectors")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgperm, ident.size() * 4, "difference order")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgkq, kid.size() * 4, "k map")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgg0, zero.size() * 4, "zero umklapp")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgrd, (size_t)ntd * nd * cb, "diagonal densities")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgw, wbar.size() * 8, "extrapolar weights")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgP, (size_t)nw * nd * 16, "extrapolar term")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_bgidx, didx.size() * 4, "difference index")) != CHI0_OK) return s;
+  CK(cudaMemcpyAsync(c->d_bgd.p, dflat.data(), dflat.size() * 4, cudaMemcpyHostToDevice, c->st), "d H2D");
+  CK(cudaMemcpyAsync(c->d_bgperm.p, ident.data(), ident.size() * 4, cudaMemcpyHostToDevice, c->st), "order H2D");
+  CK(cudaMemcpyAsync(c->d_bgkq.p, kid.data(), kid.size() * 4, cudaMemcpyHostToDevice, c->st), "k map H2D");
+  CK(cudaMemcpyAsync(c->d_bgg0.p, zero.data(), zero.size() * 4, cudaMemcpyHostToDevice, c->st), "G0 H2D");
+  CK(cudaMemcpyAsync(c->d_bgw.p, wbar.data(), wbar.size() * 8, cudaMemcpyHostToDevice, c->st), "wbar H2D");
+  CK(cudaMemcpyAsync(c->d_bgidx.p, didx.data(), didx.size() * 4, cudaMemcpyHostToDevice, c->st), "index H2D");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  c->bg_nd = nd;
+  c->bg_ntd = ntd;
+  c->bg_ch = ch;
+  return CHI0_OK;
+}
+
+// diagonal densities (rho kernel, same-band mode) and their weighted sum
+// P[w][d]; independent of the contraction, so launched before it (the
+// Hermitised gather into chi0 follows each frequency's reduction)
+chi0_status launch_bg(chi0_ctx* c) {
+  const RhoGeom& g = c->geom;
+  const int ng = c->cfg.ng, nw = c->cfg.nw;
+  const size_t cb = cplx_bytes(c);
+  chi0::stage_begin(c, CHI0_STAGE_RHO);
+  for (int k = 0; k < c->bg_ch.n; ++k) {
+    const RhoGeom& gc = c->bg_geom[k];
+    const int32_t* dset = (const int32_t*)c->d_bgd.p + 3 * (size_t)c->bg_ch.start[k];
+    char* out = (char*)c->d_bgrd.p + (size_t)c->bg_ch.off[k] * cb;
+    cudaError_t e;
+    if (c->fp64)
+      e = chi0::launch_rho_pairs<double, double2>(gc, (const double2*)c->d_U.p, (const int32_t*)c->d_bgkq.p,
+                                                  (const int32_t*)c->d_bgg0.p, dset,
+                                                  (const int32_t*)c->d_bgperm.p, (const double2*)c->d_tw1.p,
+                                                  (const double2*)c->d_tw2.p, (double2*)out, c->st);
+    else
+      e = chi0::launch_rho_pairs<float, float2>(gc, (const float2*)c->d_U.p, (const int32_t*)c->d_bgkq.p,
+                                                (const int32_t*)c->d_bgg0.p, dset,
+                                                (const int32_t*)c->d_bgperm.p, (const float2*)c->d_tw1.p,
+                                                (const float2*)c->d_tw2.p, (float2*)out, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "extrapolar densities launch");
+  }
+  chi0::stage_end(c, CHI0_STAGE_RHO, c->bg_ch.n);
+  (void)g;
+  chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+  cudaError_t e = c->fp64 ? chi0::launch_bg_sum<double2>((const double2*)c->d_bgrd.p, c->bg_ch,
+                                                        (const double*)c->d_bgw.p, c->bg_ntd, c->bg_nd, nw,
+                                                        (double2*)c->d_bgP.p, c->st)
+                          : chi0::launch_bg_sum<float2>((const float2*)c->d_bgrd.p, c->bg_ch,
+                                                       (const double*)c->d_bgw.p, c->bg_ntd, c->bg_nd, nw,
+                                                       (double2*)c->d_bgP.p, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "extrapolar term launch");
+  chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+  return CHI0_OK;
+}
+
 chi0_status plan_chi0(chi0_ctx* c, int iq) {
   if (iq != c->plan_rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
   const int nw = c->cfg.nw, ng = c->cfg.ng;
@@ -415,6 +569,7 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
       if ((s = chi0::tc_plan(c, c->nt, ng, nw)) != CHI0_OK) return s;
     }
     if (c->term_params && (s = chi0::term_plan(c, iq)) != CHI0_OK) return s;
+    if (c->bg_on && (s = plan_bg(c)) != CHI0_OK) return s;
   }
   c->plan_chi_iq = iq;
   return CHI0_OK;
@@ -435,7 +590,7 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
     cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
                                          (const double*)c->d_eps.p, (const double*)c->d_occ.p,
                                          (const double*)c->d_omim.p, nullptr, nw, c->cfg.eta, pref,
-                                         c->cfg.occ_drop_tol, (double*)c->d_w.p, c->st);
+                                         c->cfg.occ_drop_tol, c->bg_on, c->bg_eps, (double*)c->d_w.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
     chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
@@ -445,6 +600,8 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
     c->stage[CHI0_STAGE_CONTRACT].bytes = (double)c->nt * ng * cplx_bytes(c) + (double)c->nt * nw * 8;
     c->stage[CHI0_STAGE_REDUCE].bytes = (double)n2 * nw * 16;
     c->stage[CHI0_STAGE_REDUCE].flops = 0;
+    if (c->bg_on && (s = launch_bg(c)) != CHI0_OK) return s;
+    const chi0::BgApply bga{(const double2*)c->d_bgP.p, (const int32_t*)c->d_bgidx.p, c->bg_nd};
     if (c->fp64) {
       chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
       e = chi0::launch_chi0_fp64_partials((const double2*)c->d_R.p, (const double*)c->d_w.p, c->nt, ng,
@@ -457,9 +614,16 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
       if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch");
       chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
       c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
+      if (c->bg_on) {
+        chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+        e = chi0::launch_bg_apply(bga.P, bga.didx, ng, bga.nd, nw, (double2*)c->d_chi.p, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "extrapolar term launch");
+        chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+      }
     } else {
       s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p,
-                          c->term_params ? nullptr : ev_freq, c->term_params ? nullptr : ev_prep);
+                          c->term_params ? nullptr : ev_freq, c->term_params ? nullptr : ev_prep,
+                          c->bg_on ? &bga : nullptr);
       if (s != CHI0_OK) return s;
     }
     if (c->term_params) {
@@ -546,8 +710,8 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   chi0_status s;
   if (c->fp64 || c->term_params || c->nt == 0 || nw < 2) {
-    // FP64 contraction and Dyson share the FP64 pipe; the terminator needs
-    // every frequency of chi0 first: no overlap to gain
+    // FP64 contraction and Dyson share the FP64 pipe; the learned terminator
+    // needs every frequency of chi0 first: no overlap to gain
     if ((s = launch_chi0(c)) != CHI0_OK) return s;
     return launch_eps(c);
   }
@@ -825,6 +989,19 @@ chi0_status chi0_build_invert(chi0_ctx* c, int iq, void* chi_out, void* eps_out,
   return CHI0_OK;
 }
 
+chi0_status chi0_set_bg_terminator(chi0_ctx* c, int on, double eps_bar) {
+  if (!c) return CHI0_EINVAL;
+  if (on && !std::isfinite(eps_bar)) return fail(c, CHI0_EINVAL, "extrapolar energy must be finite");
+  if (on && c->term_params)
+    return fail(c, CHI0_EINVAL, "the learned terminator is set: the two corrections exclude each other");
+  c->bg_on = on ? 1 : 0;
+  c->bg_eps = eps_bar;
+  // the transition block changes (every band n): compute_rho must run again
+  c->rho_iq = c->chi_iq = c->eps_iq = -1;
+  c->plan_rho_iq = c->plan_chi_iq = c->plan_eps_iq = -1;
+  return CHI0_OK;
+}
+
 chi0_status chi0_get_response_gvectors(chi0_ctx* c, int iq, int32_t* out) {
   if (!c) return CHI0_EINVAL;
   if (iq < 0 || iq >= c->cfg.nq || !out) return fail(c, CHI0_EINVAL, "bad iq or NULL out");
@@ -941,7 +1118,8 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_gresp, &c->d_gperm, &c->d_kq, &c->d_g0, &c->d_tw1, &c->d_tw2, &c->d_U, &c->d_R,
                     &c->d_w, &c->d_part, &c->d_chi, &c->d_A, &c->d_colp, &c->d_rowp, &c->d_pinv,
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
-                    &c->d_termq, &c->d_termw, &c->d_termc};
+                    &c->d_termq, &c->d_termw, &c->d_termc, &c->d_bgd, &c->d_bgperm, &c->d_bgkq,
+                    &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)

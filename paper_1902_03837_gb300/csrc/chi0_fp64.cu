@@ -21,7 +21,7 @@ namespace {
 __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* __restrict__ kq,
                           const double* __restrict__ eps, const double* __restrict__ occ,
                           const double* __restrict__ omega_im, int nw, double eta, double pref,
-                          double occ_tol, double* __restrict__ w) {
+                          double occ_tol, int bg, double eps_bar, double* __restrict__ w) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
@@ -32,12 +32,18 @@ __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_
   const int ikp = kq[ik];
   const double df = occ[(size_t)ikp * nb + m] - occ[(size_t)ik * nb + n];
   const double d = eps[(size_t)ikp * nb + m] - eps[(size_t)ik * nb + n];
+  const double fm = occ[(size_t)ikp * nb + m];
+  const double dbar = eps[(size_t)ikp * nb + m] - eps_bar;  // m into an empty state at eps_bar
   for (int iw = 0; iw < nw; ++iw) {
     double v = 0.0;
+    const double s = omega_im[iw] + eta;
     if (df > occ_tol) {
-      const double s = omega_im[iw] + eta;
       const double den = d * d + s * s;
       v = den > 0.0 ? pref * df * (2.0 * d / den) : 0.0;
+    }
+    if (bg && fm > occ_tol) {
+      const double den = dbar * dbar + s * s;
+      if (den > 0.0) v -= pref * fm * (2.0 * dbar / den);
     }
     w[(size_t)iw * nt + t] = v;
   }
@@ -143,12 +149,12 @@ __global__ void k_chi0_reduce(const double2* __restrict__ part, int nchunks, int
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
                            const double* eps, const double* occ, const double* omega_im,
                            const double* /*omega_re*/, int nw, double eta, double pref,
-                           double occ_tol, double* w, cudaStream_t s) {
+                           double occ_tol, int bg, double eps_bar, double* w, cudaStream_t s) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   if (nt == 0) return cudaSuccess;
   const int64_t blocks = (nt + 255) / 256;
   k_weights<<<(unsigned)blocks, 256, 0, s>>>(nk, n_lo, Nn, Nm, nb, kq, eps, occ, omega_im, nw, eta,
-                                            pref, occ_tol, w);
+                                            pref, occ_tol, bg, eps_bar, w);
   return cudaGetLastError();
 }
 

@@ -53,6 +53,14 @@ struct chi0_ctx {
   const float* term_params = nullptr;  // device parameters; NULL = off
   int term_bf16 = 1;
   DevBuf d_termx, d_termy, d_termq, d_termw, d_termc;
+  // Bruneval-Gonze extrapolar correction (bgterm.cu, plan in chi0_api.cu)
+  int bg_on = 0;
+  double bg_eps = 0.0;                 // extrapolar energy (Ha)
+  int bg_nd = 0;                       // difference vectors d = G_i - G_j
+  int64_t bg_ntd = 0;                  // states (k, m < Nm) with diagonal densities
+  std::vector<RhoGeom> bg_geom;        // rho geometry of each chunk of the difference set
+  chi0::BgChunks bg_ch{};
+  DevBuf d_bgd, d_bgperm, d_bgkq, d_bgg0, d_bgrd, d_bgw, d_bgP, d_bgidx;
 
   // per-stage device time: CUDA event pairs on the context's stream, summed
   // over every launch of the stage since the last chi0_get_stats
@@ -89,9 +97,10 @@ void stage_end(chi0_ctx* c, int stage, int kernels);
 chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw);
 // ev_freq (optional, [nw]): event w is recorded once chi of frequency w is final;
 // ev_prep (optional, [nw]): event w once the operand of frequency w is split
+// bg (optional): the extrapolar term added to each frequency after its reduction
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq = nullptr,
-                      const cudaEvent_t* ev_prep = nullptr);
+                      const cudaEvent_t* ev_prep = nullptr, const chi0::BgApply* bg = nullptr);
 void tc_release(chi0_ctx* c);
 // learned terminator: network kernels and the correction of a built chi0
 int mlp_nparams();

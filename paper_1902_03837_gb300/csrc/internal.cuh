@@ -30,6 +30,8 @@ struct RhoGeom {
   int Nm;                  // m bands (at k - q): [0, Nm)
   int g0max;               // largest |G0_a| over the k-pairs (umklapp)
   int g0z_min, g0z_max;    // range of G0_z over the k-pairs
+  int diag;                // 1: the m grid is band n_lo + n at the same k (Nm = 1):
+                           // diagonal densities <n k| e^{i G.r} |n k>
 };
 
 // Zero padding of the n plane in the rho kernel's shared memory.
@@ -88,10 +90,37 @@ cudaError_t launch_rho_batch(const RhoTask<T, TOUT>* tasks_dev, int ntasks, int6
                              size_t smem, unsigned long long* counter, int nsm, cudaStream_t s);
 
 // a3: real transition weights w[iw][t] (FP64).
+// With bg != 0 each weight is reduced by the extrapolar weight of its m
+// (a transition from m into an empty state at eps_bar): the closure form of
+// the Bruneval-Gonze correction.
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
                            const double* eps, const double* occ, const double* omega_im,
                            const double* omega_re, int nw, double eta, double pref,
-                           double occ_tol, double* w, cudaStream_t s);
+                           double occ_tol, int bg, double eps_bar, double* w, cudaStream_t s);
+
+// Bruneval-Gonze correction, the two steps after the contraction:
+// P[iw][d] = sum_t wbar[iw][t] rd(t, d) over the diagonal densities rd of the
+// states t = (k, m) on the difference vectors d (stored in chunks: chunk c
+// holds d in [start[c], start[c + 1]) as [t][d - start[c]] at offset off[c]),
+// then chi[iw][i][j] += P[iw][didx[i][j]] (Hermitised).
+constexpr int kBgMaxChunks = 16;
+struct BgChunks {
+  int n;
+  int start[kBgMaxChunks + 1];
+  int64_t off[kBgMaxChunks];
+};
+template <typename TOUT>
+cudaError_t launch_bg_sum(const TOUT* rd, const BgChunks& ch, const double* wbar, int64_t ntd, int nd,
+                          int nw, double2* P, cudaStream_t s);
+cudaError_t launch_bg_apply(const double2* P, const int32_t* didx, int ng, int nd, int nw, double2* chi,
+                            cudaStream_t s);
+// The extrapolar term of every frequency, applied by the contraction right
+// after its own reduction of that frequency (before its per-frequency event).
+struct BgApply {
+  const double2* P;      // [nw][nd]
+  const int32_t* didx;   // [ng][ng]
+  int nd;
+};
 
 // a4 (FP64 form): split-K partials of chi0 = sum_t w_t R_t R_t^H, lower
 // triangle tiles; part[kc][iw][i][j] (complex128).

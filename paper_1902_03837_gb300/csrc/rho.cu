@@ -350,7 +350,7 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
   }
 
   const T2* Un = U + ((size_t)ik * g.nb + (g.n_lo + nrel)) * ((size_t)g.N1 * plane);
-  const T2* Um = U + ((size_t)ikp * g.nb + m0) * ((size_t)g.N1 * plane);
+  const T2* Um = U + ((size_t)ikp * g.nb + m0 + (g.diag ? g.n_lo + nrel : 0)) * ((size_t)g.N1 * plane);
   const size_t band_stride = (size_t)g.N1 * plane;
   const int nhb = (HZ + kHZT - 1) / kHZT;
   const int nyb = (HY + kHYT - 1) / kHYT;
@@ -714,6 +714,7 @@ cudaError_t rho_task_make(const RhoGeom& g, const typename C2<T>::t* U, const in
   sm.unp_rows = max(sm.padz + hz_max + g.NZ, sm.padz + g.NZ);
   const int cap = kRhoThreads * kAccMax;
   int jm = jm_max;
+  while (jm > 1 && jm > g.Nm) jm /= 2;  // no wider than the m bands there are
   while (jm > 1 && jm * g.ng > cap) jm /= 2;
   if (jm * g.ng > cap) return cudaErrorInvalidValue;  // ng > 4096
   *smem = rho_smem_bytes<T>(g, sm, jm_max);

@@ -593,7 +593,8 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
 }
 
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
-                      double2* chi, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep) {
+                      double2* chi, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep,
+                      const BgApply* bg) {
   if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "tensor-core contraction not planned");
   TcState& t = *static_cast<TcState*>(c->tc);
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
@@ -630,7 +631,8 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       stage_begin(c, CHI0_STAGE_REDUCE);
       k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
           (const double2*)t.part.p, t.nchunks, t.ntiles, ng, chi + (size_t)iw * n2);
-      stage_end(c, CHI0_STAGE_REDUCE, 1);
+      if (bg) launch_bg_apply(bg->P + (size_t)iw * bg->nd, bg->didx, ng, bg->nd, 1, chi + (size_t)iw * n2, c->st);
+      stage_end(c, CHI0_STAGE_REDUCE, bg ? 2 : 1);
       if (ev_freq) cudaEventRecord(ev_freq[iw], c->st);
     }
   }

@@ -446,6 +446,8 @@ chi0_status chi0_term_features(chi0_ctx* c, int iq, const void* chi_trunc, const
 
 chi0_status chi0_set_terminator(chi0_ctx* c, const float* params, int bf16) {
   if (!c) return CHI0_EINVAL;
+  if (params && c->bg_on)
+    return chi0::ctx_fail(c, CHI0_EINVAL, "the extrapolar terminator is set: the two corrections exclude each other");
   c->term_params = params;
   c->term_bf16 = bf16;
   c->chi_iq = c->eps_iq = -1;

@@ -12,6 +12,7 @@ from .systems import (  # noqa: F401
     SystemSpec,
     System,
     make_system,
+    make_closure_system,
     make_plane_wave_system,
     truncate_bands,
     cfg_learned,

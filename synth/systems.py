@@ -338,3 +338,47 @@ def cfg_learned(seed: int = 4000, full_bands: int = 800, n_occ: int = 12, kgrid=
     return SystemSpec(a=10.0, kgrid=tuple(kgrid), n_occ=n_occ, n_bands=full_bands, kc=kc,
                       fft=tuple(fft), ng=ng, q_frac=(q,), freqs=tuple(gauss_legendre_freqs(nw, 0.0, 100.0)),
                       eta=0.0, seed=seed, coef_dtype="c64")
+
+
+def make_closure_system(seed: int = 5, L: int = 3, L_occ: int = 1, n_occ: int = 2, nb_keep: int = 12,
+                        omitted_ev=(45.0, 45.0), ng: int = 7, fft=(16, 16, 16),
+                        freqs=(0.3j, 2.0j), coef_dtype: str = "c128") -> System:
+    """A two-k system whose band basis is complete: at each k the plane waves
+    are every G with |G_a| <= L and there are as many bands, from a random
+    unitary matrix.  The occupied bands are built from G with |G_a| <= L_occ
+    only, so with response vectors and umklapp vectors within |G_a| <= 1 every
+    product of an occupied state with e^{i(q+G).r} stays inside the basis.
+    Energies: occupied uniform in [-10, 0] eV, bands n_occ..nb_keep-1 uniform
+    in [1, 30] eV (sorted), the rest uniform in omitted_ev (eV; equal ends put
+    them all at one energy).  q = (1/2, 0, 0) on a 2 x 1 x 1 grid.  No
+    time-reversal pairing is imposed: the identities this system serves
+    (closure over a complete band set) do not need it."""
+    rng = np.random.default_rng(seed)
+    v = np.arange(-L, L + 1)
+    g = np.stack(np.meshgrid(v, v, v, indexing="ij"), axis=-1).reshape(-1, 3)
+    npw = g.shape[0]
+    inner = np.nonzero(np.all(np.abs(g) <= L_occ, axis=1))[0]
+    nk = 2
+    coef = np.zeros((nk, npw, npw), dtype=np.complex128)
+    eps = np.zeros((nk, npw))
+    occ = np.zeros((nk, npw))
+    for ik in range(nk):
+        M = rng.standard_normal((npw, npw)) + 1j * rng.standard_normal((npw, npw))
+        M[:, :n_occ] = 0.0
+        M[inner, :n_occ] = (rng.standard_normal((inner.size, n_occ))
+                            + 1j * rng.standard_normal((inner.size, n_occ)))
+        Q, _ = np.linalg.qr(M)  # orthonormal columns, the first n_occ on the inner cube
+        coef[ik] = Q.T
+        eps[ik, :n_occ] = rng.uniform(-10.0, 0.0, n_occ) / HA_EV
+        eps[ik, n_occ:nb_keep] = np.sort(rng.uniform(1.0, 30.0, nb_keep - n_occ)) / HA_EV
+        eps[ik, nb_keep:] = rng.uniform(omitted_ev[0], omitted_ev[1], npw - nb_keep) / HA_EV
+        occ[ik, :n_occ] = 1.0
+    if coef_dtype == "c64":
+        coef = coef.astype(np.complex64)
+    spec = SystemSpec(a=6.0, kgrid=(2, 1, 1), n_occ=n_occ, n_bands=npw, fft=tuple(fft), ng=ng,
+                      q_frac=((0.5, 0.0, 0.0),), freqs=tuple(freqs), eta=0.0, seed=seed, coef_dtype=coef_dtype)
+    return System(spec=spec, lattice=6.0 * np.eye(3), omega_cell=216.0,
+                  kfrac=np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]]), npw=np.full(nk, npw, dtype=np.int32),
+                  gvec=np.broadcast_to(g, (nk, npw, 3)).astype(np.int32).copy(), coef=coef, eps=eps, occ=occ,
+                  q_frac=np.array(spec.q_frac), freqs=np.array(spec.freqs), eta=0.0, spin_factor=2.0,
+                  fft=spec.fft, ng=spec.ng)

@@ -11,13 +11,11 @@
    truncated chi0 plus the correction equals the full-band chi0;
 4. the correction is Hermitian on the imaginary axis.
 """
-import dataclasses
-
 import numpy as np
 import pytest
 
 import oracle as O
-from synth import HA_EV, System, SystemSpec, cfg_tiny, make_system, truncate_bands
+from synth import HA_EV, cfg_tiny, make_closure_system, make_system, truncate_bands
 
 
 def _small():
@@ -51,47 +49,10 @@ def test_diag_density_real_space_definition():
         assert np.allclose(got, ref, atol=1e-12), (m, got, ref)
 
 
-def _cube(L):
-    v = np.arange(-L, L + 1)
-    return np.stack(np.meshgrid(v, v, v, indexing="ij"), axis=-1).reshape(-1, 3)
-
-
-def _closure_system(eps_bar, nb_keep, seed=5):
-    """Complete basis (all G with |G_a| <= 3, 343 bands at each k); occupied
-    states built from G with |G_a| <= 1; bands >= nb_keep at eps_bar."""
-    rng = np.random.default_rng(seed)
-    kgrid = (2, 1, 1)
-    g = _cube(3)
-    npw = g.shape[0]
-    inner = np.nonzero(np.all(np.abs(g) <= 1, axis=1))[0]
-    n_occ = 2
-    nk = 2
-    coef = np.zeros((nk, npw, npw), dtype=np.complex128)
-    eps = np.zeros((nk, npw))
-    occ = np.zeros((nk, npw))
-    for ik in range(nk):
-        M = rng.standard_normal((npw, npw)) + 1j * rng.standard_normal((npw, npw))
-        M[:, :n_occ] = 0.0
-        M[inner, :n_occ] = rng.standard_normal((inner.size, n_occ)) + 1j * rng.standard_normal((inner.size, n_occ))
-        Q, _ = np.linalg.qr(M)                    # columns: orthonormal basis, first two on the inner cube
-        coef[ik] = Q.T
-        eps[ik, :n_occ] = rng.uniform(-10.0, 0.0, n_occ) / HA_EV
-        eps[ik, n_occ:nb_keep] = np.sort(rng.uniform(1.0, 30.0, nb_keep - n_occ)) / HA_EV
-        eps[ik, nb_keep:] = eps_bar
-        occ[ik, :n_occ] = 1.0
-    spec = SystemSpec(a=6.0, kgrid=kgrid, n_occ=n_occ, n_bands=npw, fft=(16, 16, 16), ng=7,
-                      q_frac=((0.5, 0.0, 0.0),), freqs=(0.3j, 2.0j), eta=0.0)
-    return System(spec=spec, lattice=6.0 * np.eye(3), omega_cell=216.0,
-                  kfrac=np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]]), npw=np.full(nk, npw, dtype=np.int32),
-                  gvec=np.broadcast_to(g, (nk, npw, 3)).astype(np.int32).copy(), coef=coef, eps=eps, occ=occ,
-                  q_frac=np.array(spec.q_frac), freqs=np.array(spec.freqs), eta=0.0, spin_factor=2.0,
-                  fft=spec.fft, ng=spec.ng)
-
-
 def test_closure_exact_reproduces_full_band_sum():
     eps_bar = 45.0 / HA_EV
     nb_keep = 12
-    full = _closure_system(eps_bar, nb_keep)
+    full = make_closure_system(nb_keep=nb_keep, omitted_ev=(eps_bar * HA_EV, eps_bar * HA_EV))
     G = O.response_gvectors(full.spec.kgrid, full.q_frac[0], full.ng)
     assert np.abs(G).max() <= 1
     _, g0 = O.kpair_map(full.spec.kgrid, full.q_frac[0])
