@@ -120,17 +120,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def build_system(kgrid=None, nw=32):
-    """The precision workload; kgrid / nw override it for smaller profiling runs."""
-    from synth import cfg_precision, make_system
+def build_system(kgrid=None, nw=32, real_axis=False):
+    """The precision workload; kgrid / nw override it for smaller profiling
+    runs; real_axis puts its nw frequencies on the real axis instead (evenly
+    spaced on (0, 100] eV, broadening 0.1 eV)."""
+    import dataclasses
+    from synth import HA_EV, cfg_precision, make_system
     spec = cfg_precision(nw=nw)
     if kgrid is not None:
         spec.kgrid = tuple(kgrid)
+    if real_axis:
+        w = np.arange(1, nw + 1) * (100.0 / nw) / HA_EV
+        spec = dataclasses.replace(spec, freqs=tuple(complex(x, 0.0) for x in w), eta=0.1 / HA_EV)
     return make_system(spec)
 
 
 def workload_name(args):
     base = _workload_base(args)
+    if getattr(args, "real_axis", False):
+        base = base.replace(" imaginary GL frequencies in [0,100] eV", " real frequencies on (0,100] eV, eta 0.1 eV")
     if getattr(args, "bg_terminator", None) is not None:
         base += f", Bruneval-Gonze extrapolar correction at {args.bg_terminator:g} eV"
     return base
@@ -203,7 +211,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    s = build_system(args.kgrid, args.nw)
+    s = build_system(args.kgrid, args.nw, args.real_axis)
     ng, nw = s.ng, s.freqs.size
     prec = lib.CHI0_MIXED_BF16X3 if args.precision == "mixed" else lib.CHI0_FP64
     ctx = lib.Chi0.for_system(s, precision=prec, stream=stream.cuda_stream)
@@ -315,7 +323,8 @@ def run_ours(args, rank, world, dist):
         mpad = -(-2 * ng // 128) * 128
         kpad = -(-nt // 64) * 64
         nT = mpad // 128
-        issued = 3 * 2 * 128 * 128 * (nT * (nT + 1) // 2) * kpad * nw
+        ncontract = nw * (2 if args.real_axis else 1)  # a real frequency is two Hermitian contractions
+        issued = 3 * 2 * 128 * 128 * (nT * (nT + 1) // 2) * kpad * ncontract
         extra = {"issued_tflops": issued / (per_step_ms[dom] * 1e-3) / 1e12,
                  "issued_frac": issued / (per_step_ms[dom] * 1e-3) / 1e12 / peak}
     elif bound == "fp64":
@@ -370,6 +379,9 @@ def main():
                     help="mixed: FP32 rho, BF16x3 tensor-core chi0, FP64 Dyson (default); "
                          "fp64: the plain FP64 form of every step, for the speedup comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--real-axis", action="store_true",
+                    help="real frequencies on (0, 100] eV with 0.1 eV broadening (two contractions each, "
+                         "general Dyson step)")
     ap.add_argument("--bg-terminator", type=float, default=None, metavar="EV",
                     help="apply the Bruneval-Gonze extrapolar correction with this extrapolar energy (eV)")
     args = ap.parse_args()

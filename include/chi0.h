@@ -87,7 +87,11 @@ typedef struct {
   const double* q_frac;   /* [nq][3] reduced coordinates; each q must be a vector of the k grid;
                              copied at chi0_create */
   int nw;                 /* number of frequencies */
-  const double* omega;    /* [nw][2] complex frequencies (re, im) in Ha; copied at chi0_create */
+  const double* omega;    /* [nw][2] complex frequencies (re, im) in Ha; copied at chi0_create.
+                             Either imaginary-axis (re = 0: chi0 Hermitian) or real-axis (im = 0,
+                             re > 0, and eta > 0: complex weights, chi0 = H_r + i H_i from two
+                             Hermitian contractions, eps~ inverted by general Gauss-Jordan);
+                             other forms give CHI0_EUNSUPPORTED at chi0_build_chi0 */
   double eta;             /* Ha; +i*eta on both poles (retarded); 0 on the imaginary axis */
   double spin_factor;     /* f_s: 2 without spin polarisation, 1 with it */
   int precision;          /* chi0_precision */
@@ -139,7 +143,11 @@ chi0_status chi0_build_chi0(chi0_ctx* ctx, int iq, void* out, int out_on_device)
 
 /* eps~^-1(q_iq, w) = (1 - v^1/2 chi0 v^1/2)^-1 for every frequency, Eqs.
  * (X_rpa), (X_rpa_inv) in the symmetric form of Eq. (W_def), by FP64
- * Gauss-Jordan elimination (eps~ is Hermitian positive definite here).
+ * Gauss-Jordan elimination without pivoting: on the imaginary axis eps~ is
+ * Hermitian positive definite (lower tiles only, Hermitian sweep rule); on
+ * the real axis (w > 0, eta > 0) eps~ has a positive semidefinite imaginary
+ * part, inherited by every Schur complement, and the elimination runs over
+ * every tile.
  * out: [nw][ng][ng] complex128 as for chi0_build_chi0 (NULL not allowed).
  * Requires chi0_build_chi0(iq).  A vanishing pivot is reported as CHI0_ENOTPD
  * by the next synchronising call.  Errors: CHI0_ESTATE, CHI0_EINVAL,

@@ -189,7 +189,7 @@ chi0_status check_device_error(chi0_ctx* c) {
   if (h[0] || h[1]) {
     CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(h), c->st), "clear error flag");
     if (h[1]) return fail(c, CHI0_ETIMEOUT, "a bounded device-side wait gave up (code %d)", h[1]);
-    return fail(c, CHI0_ENOTPD, "Dyson elimination met a non-positive pivot: eps~ not HPD");
+    return fail(c, CHI0_ENOTPD, "Dyson elimination met a non-positive (Hermitian) or vanishing (general) pivot");
   }
   return CHI0_OK;
 }
@@ -383,12 +383,27 @@ chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
   return CHI0_OK;
 }
 
+// Frequency factor of a transition with energy difference d (the weights
+// kernel's form): kind 0 the imaginary axis, kinds 1 / 2 the real / imaginary
+// part on the real axis.
+static double pole_weight_host(int kind, double om, double eta, double d) {
+  if (kind == 0) {
+    const double sw = om + eta;
+    const double den = d * d + sw * sw;
+    return den > 0.0 ? 2.0 * d / den : 0.0;
+  }
+  const double a = om + d, b = om - d;
+  const double da = a * a + eta * eta, db = b * b + eta * eta;
+  if (!(da > 0.0) || !(db > 0.0)) return 0.0;
+  return kind == 1 ? a / da - b / db : eta / db - eta / da;
+}
+
 // ---- Bruneval-Gonze extrapolar correction: planning and launch
 // Difference vectors d = G_i - G_j of the response set, ordered by (y, z, x)
 // (the order the rho kernel visits its G set in), cut into chunks of at most
 // 4096 (the rho kernel's register accumulators at one m band per block).
 chi0_status plan_bg(chi0_ctx* c) {
-  const int ng = c->cfg.ng, nw = c->cfg.nw;
+  const int ng = c->cfg.ng, nw = c->nwv;
   const RhoGeom& g = c->geom;
   auto less_yzx = [](const std::array<int32_t, 3>& A, const std::array<int32_t, 3>& B) {
     if (A[1] != B[1]) return A[1] < B[1];
@@ -456,17 +471,15 @@ chi0_status plan_bg(chi0_ctx* c) {
   const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
   const double tol = c->cfg.occ_drop_tol;
   std::vector<double> wbar((size_t)nw * ntd, 0.0);
-  for (int iw = 0; iw < nw; ++iw) {
-    const double sw = c->om[2 * iw + 1] + c->cfg.eta;
+  for (int iw = 0; iw < nw; ++iw)
     for (int ik = 0; ik < c->nk; ++ik)
       for (int m = 0; m < c->Nm; ++m) {
         const double f = c->h_occ[(size_t)ik * c->nb + m];
         if (!(f > tol)) continue;
         const double dbar = c->h_eps[(size_t)ik * c->nb + m] - c->bg_eps;
-        const double den = dbar * dbar + sw * sw;
-        if (den > 0.0) wbar[(size_t)iw * ntd + (size_t)ik * c->Nm + m] = pref * f * (2.0 * dbar / den);
+        wbar[(size_t)iw * ntd + (size_t)ik * c->Nm + m] =
+            pref * f * pole_weight_host(c->h_vkind[iw], c->h_vval[iw], c->cfg.eta, dbar);
       }
-  }
   std::vector<int32_t> dflat((size_t)nd * 3), ident(std::min(nd, kChunk)), kid(c->nk), zero((size_t)c->nk * 3, 0);
   for (int e = 0; e < nd; ++e)
     for (int a = 0; a < 3; ++a) dflat[(size_t)e * 3 + a] = D[e][a];
@@ -500,7 +513,7 @@ chi0_status plan_bg(chi0_ctx* c) {
 // Hermitised gather into chi0 follows each frequency's reduction)
 chi0_status launch_bg(chi0_ctx* c) {
   const RhoGeom& g = c->geom;
-  const int ng = c->cfg.ng, nw = c->cfg.nw;
+  const int ng = c->cfg.ng, nw = c->nwv;
   const size_t cb = cplx_bytes(c);
   chi0::stage_begin(c, CHI0_STAGE_RHO);
   for (int k = 0; k < c->bg_ch.n; ++k) {
@@ -536,13 +549,46 @@ chi0_status launch_bg(chi0_ctx* c) {
 
 chi0_status plan_chi0(chi0_ctx* c, int iq) {
   if (iq != c->plan_rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
-  const int nw = c->cfg.nw, ng = c->cfg.ng;
-  for (int iw = 0; iw < nw; ++iw)
-    if (c->om[2 * iw] != 0.0)
-      return fail(c, CHI0_EUNSUPPORTED, "frequency %d has a real part: non-Hermitian chi0 not supported", iw);
+  const int nw0 = c->cfg.nw, ng = c->cfg.ng;
+  // frequency list of the contraction (see chi0_ctx::nwv)
+  c->h_vval.clear();
+  c->h_vkind.clear();
+  c->h_vr.assign(nw0, -1);
+  c->h_vi.assign(nw0, -1);
+  c->has_real = false;
+  for (int iw = 0; iw < nw0; ++iw) {
+    const double re = c->om[2 * iw], im = c->om[2 * iw + 1];
+    if (re == 0.0) {
+      c->h_vr[iw] = (int)c->h_vval.size();
+      c->h_vval.push_back(im);
+      c->h_vkind.push_back(0);
+      continue;
+    }
+    if (im != 0.0 || !(re > 0.0) || !(c->cfg.eta > 0.0))
+      return fail(c, CHI0_EUNSUPPORTED,
+                  "frequency %d: off the imaginary axis only real frequencies > 0 with eta > 0 are supported", iw);
+    c->has_real = true;
+    c->h_vr[iw] = (int)c->h_vval.size();
+    c->h_vval.push_back(re);
+    c->h_vkind.push_back(1);
+    c->h_vi[iw] = (int)c->h_vval.size();
+    c->h_vval.push_back(re);
+    c->h_vkind.push_back(2);
+  }
+  if (c->has_real && c->term_params)
+    return fail(c, CHI0_EUNSUPPORTED, "the learned terminator is for imaginary-axis frequencies only");
+  c->nwv = (int)c->h_vval.size();
+  const int nw = c->nwv;
   chi0_status s;
   const size_t n2 = (size_t)ng * ng;
-  if ((s = ensure(c, c->d_chi, n2 * nw * 16, "chi0")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_chi, n2 * nw0 * 16, "chi0")) != CHI0_OK) return s;
+  if (c->has_real) {
+    if ((s = ensure(c, c->d_chiv, n2 * nw * 16, "chi0 parts")) != CHI0_OK) return s;
+    if ((s = ensure(c, c->d_vr, (size_t)nw0 * 4, "frequency map")) != CHI0_OK) return s;
+    if ((s = ensure(c, c->d_vi, (size_t)nw0 * 4, "frequency map")) != CHI0_OK) return s;
+    CK(cudaMemcpyAsync(c->d_vr.p, c->h_vr.data(), (size_t)nw0 * 4, cudaMemcpyHostToDevice, c->st), "map H2D");
+    CK(cudaMemcpyAsync(c->d_vi.p, c->h_vi.data(), (size_t)nw0 * 4, cudaMemcpyHostToDevice, c->st), "map H2D");
+  }
   if (!c->d_err.p) {
     if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
     CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
@@ -551,9 +597,9 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
   if (c->nt > 0) {
     if ((s = ensure(c, c->d_w, (size_t)c->nt * nw * 8, "weights")) != CHI0_OK) return s;
     if ((s = ensure(c, c->d_omim, (size_t)nw * 8, "frequencies")) != CHI0_OK) return s;
-    std::vector<double> omim(nw);
-    for (int iw = 0; iw < nw; ++iw) omim[iw] = c->om[2 * iw + 1];
-    CK(cudaMemcpyAsync(c->d_omim.p, omim.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
+    if ((s = ensure(c, c->d_vkind, (size_t)nw * 4, "frequency kinds")) != CHI0_OK) return s;
+    CK(cudaMemcpyAsync(c->d_omim.p, c->h_vval.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
+    CK(cudaMemcpyAsync(c->d_vkind.p, c->h_vkind.data(), nw * 4, cudaMemcpyHostToDevice, c->st), "kinds H2D");
     CK(cudaStreamSynchronize(c->st), "synchronize");
     if (c->fp64) {
       // split the transitions into chunks so that the grid fills the GPU
@@ -579,18 +625,21 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
 chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep) {
   const int iq = c->plan_chi_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "chi0 not planned");
-  const int nw = c->cfg.nw, ng = c->cfg.ng;
+  const int nw0 = c->cfg.nw, nw = c->nwv, ng = c->cfg.ng;
   const size_t n2 = (size_t)ng * ng;
   chi0_status s;
   if (c->nt == 0) {
-    CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw * 16, c->st), "zero chi0");
+    CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw0 * 16, c->st), "zero chi0");
   } else {
+    // the contraction's output: chi0 itself, or its parts H_r, H_i per real frequency
+    double2* chiv = c->has_real ? (double2*)c->d_chiv.p : (double2*)c->d_chi.p;
     const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
     chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
     cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
                                          (const double*)c->d_eps.p, (const double*)c->d_occ.p,
-                                         (const double*)c->d_omim.p, nullptr, nw, c->cfg.eta, pref,
-                                         c->cfg.occ_drop_tol, c->bg_on, c->bg_eps, (double*)c->d_w.p, c->st);
+                                         (const double*)c->d_omim.p, (const int*)c->d_vkind.p, nw, c->cfg.eta,
+                                         pref, c->cfg.occ_drop_tol, c->bg_on, c->bg_eps, (double*)c->d_w.p,
+                                         c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
     chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
@@ -609,22 +658,28 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
       if (e != cudaSuccess) return cuda_fail(c, e, "chi0 fp64 launch");
       chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
       chi0::stage_begin(c, CHI0_STAGE_REDUCE);
-      e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw,
-                                   (double2*)c->d_chi.p, c->st);
+      e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw, chiv, c->st);
       if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch");
       chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
       c->stage[CHI0_STAGE_REDUCE].bytes += (double)n2 * nw * c->nchunks * 16;
       if (c->bg_on) {
         chi0::stage_begin(c, CHI0_STAGE_REDUCE);
-        e = chi0::launch_bg_apply(bga.P, bga.didx, ng, bga.nd, nw, (double2*)c->d_chi.p, c->st);
+        e = chi0::launch_bg_apply(bga.P, bga.didx, ng, bga.nd, nw, chiv, c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "extrapolar term launch");
         chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
       }
     } else {
-      s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, (double2*)c->d_chi.p,
+      s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, chiv,
                           c->term_params ? nullptr : ev_freq, c->term_params ? nullptr : ev_prep,
                           c->bg_on ? &bga : nullptr);
       if (s != CHI0_OK) return s;
+    }
+    if (c->has_real) {
+      chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+      e = chi0::launch_combine_freq(chiv, (const int*)c->d_vr.p, (const int*)c->d_vi.p, ng, nw0,
+                                    (double2*)c->d_chi.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "frequency combine launch");
+      chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
     }
     if (c->term_params) {
       s = chi0::term_launch(c, (double2*)c->d_chi.p);
@@ -691,11 +746,25 @@ chi0_status launch_eps(chi0_ctx* c) {
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   const size_t n2 = (size_t)ng * ng;
   chi0::stage_begin(c, CHI0_STAGE_DYSON);
-  cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p, (const double*)c->d_vsqrt.p, ng, nw,
-                                     c->plan_eps_out, (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
-                                     (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
-  if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
-  chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * ((ng + 31) / 32));
+  // runs of imaginary-axis frequencies (Hermitian eps~) and of real-axis ones
+  // (general eps~), each run in one launch sequence
+  int nlaunch = 0;
+  for (int i0 = 0; i0 < nw;) {
+    const bool general = c->has_real && c->h_vi[i0] >= 0;
+    int i1 = i0 + 1;
+    while (i1 < nw && (c->has_real && c->h_vi[i1] >= 0) == general) ++i1;
+    const double2* chi = (const double2*)c->d_chi.p + (size_t)i0 * n2;
+    double2* out = c->plan_eps_out + (size_t)i0 * n2;
+    cudaError_t e = general
+        ? chi0::launch_dyson_general(chi, (const double*)c->d_vsqrt.p, ng, i1 - i0, out, (double2*)c->d_colp.p,
+                                     (double2*)c->d_rowp.p, (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st)
+        : chi0::launch_dyson(chi, (const double*)c->d_vsqrt.p, ng, i1 - i0, out, (double2*)c->d_colp.p,
+                             (double2*)c->d_rowp.p, (double2*)c->d_pinv.p, (int*)c->d_err.p, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dyson launch");
+    nlaunch += (general ? 1 : 2) + 3 * ((ng + 31) / 32);
+    i0 = i1;
+  }
+  chi0::stage_end(c, CHI0_STAGE_DYSON, nlaunch);
   // Gauss-Jordan inversion: ng^3 complex multiply-adds per frequency (about
   // half of them executed, the Hermitian lower tiles)
   c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
@@ -709,7 +778,7 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
   if (iq < 0 || c->plan_eps_iq != iq) return fail(c, CHI0_ESTATE, "build and Dyson step not planned");
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   chi0_status s;
-  if (c->fp64 || c->term_params || c->nt == 0 || nw < 2) {
+  if (c->fp64 || c->term_params || c->has_real || c->nt == 0 || nw < 2) {
     // FP64 contraction and Dyson share the FP64 pipe; the learned terminator
     // needs every frequency of chi0 first: no overlap to gain
     if ((s = launch_chi0(c)) != CHI0_OK) return s;

@@ -18,10 +18,27 @@ namespace {
 
 // w_t = pref (f_m - f_n) [1/(z + D) - 1/(z - D)] with z = w + i eta purely
 // imaginary (z = i s): the bracket is 2 D / (D^2 + s^2), real.
+// Frequency factor of one transition with energy difference d = e_m - e_n:
+//   1/(w + d + i eta) - 1/(w - d + i eta)
+// kind 0: w = i om (imaginary axis; the factor is real, 2d/(d^2 + (om+eta)^2));
+// kind 1 / 2: w = om on the real axis, the real / imaginary part.
+__device__ __forceinline__ double pole_weight(int kind, double om, double eta, double d) {
+  if (kind == 0) {
+    const double sw = om + eta;
+    const double den = d * d + sw * sw;
+    return den > 0.0 ? 2.0 * d / den : 0.0;
+  }
+  const double a = om + d, b = om - d;
+  const double da = a * a + eta * eta, db = b * b + eta * eta;
+  if (!(da > 0.0) || !(db > 0.0)) return 0.0;
+  return kind == 1 ? a / da - b / db : eta / db - eta / da;
+}
+
 __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* __restrict__ kq,
                           const double* __restrict__ eps, const double* __restrict__ occ,
-                          const double* __restrict__ omega_im, int nw, double eta, double pref,
-                          double occ_tol, int bg, double eps_bar, double* __restrict__ w) {
+                          const double* __restrict__ omega_im, const int* __restrict__ vkind, int nw,
+                          double eta, double pref, double occ_tol, int bg, double eps_bar,
+                          double* __restrict__ w) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
@@ -35,16 +52,13 @@ __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_
   const double fm = occ[(size_t)ikp * nb + m];
   const double dbar = eps[(size_t)ikp * nb + m] - eps_bar;  // m into an empty state at eps_bar
   for (int iw = 0; iw < nw; ++iw) {
+    // kind 0: imaginary-axis frequency i omega_im (+ i eta), real weight;
+    // kinds 1 / 2: real part / imaginary part of the complex weight at the
+    // real frequency omega_im[iw] with broadening eta
+    const int kind = vkind ? vkind[iw] : 0;
     double v = 0.0;
-    const double s = omega_im[iw] + eta;
-    if (df > occ_tol) {
-      const double den = d * d + s * s;
-      v = den > 0.0 ? pref * df * (2.0 * d / den) : 0.0;
-    }
-    if (bg && fm > occ_tol) {
-      const double den = dbar * dbar + s * s;
-      if (den > 0.0) v -= pref * fm * (2.0 * dbar / den);
-    }
+    if (df > occ_tol) v = pref * df * pole_weight(kind, omega_im[iw], eta, d);
+    if (bg && fm > occ_tol) v -= pref * fm * pole_weight(kind, omega_im[iw], eta, dbar);
     w[(size_t)iw * nt + t] = v;
   }
 }
@@ -148,12 +162,12 @@ __global__ void k_chi0_reduce(const double2* __restrict__ part, int nchunks, int
 
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
                            const double* eps, const double* occ, const double* omega_im,
-                           const double* /*omega_re*/, int nw, double eta, double pref,
+                           const int* vkind, int nw, double eta, double pref,
                            double occ_tol, int bg, double eps_bar, double* w, cudaStream_t s) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   if (nt == 0) return cudaSuccess;
   const int64_t blocks = (nt + 255) / 256;
-  k_weights<<<(unsigned)blocks, 256, 0, s>>>(nk, n_lo, Nn, Nm, nb, kq, eps, occ, omega_im, nw, eta,
+  k_weights<<<(unsigned)blocks, 256, 0, s>>>(nk, n_lo, Nn, Nm, nb, kq, eps, occ, omega_im, vkind, nw, eta,
                                             pref, occ_tol, bg, eps_bar, w);
   return cudaGetLastError();
 }
@@ -164,6 +178,28 @@ cudaError_t launch_chi0_fp64_partials(const double2* R, const double* w, int64_t
   const int nT = (ng + kT - 1) / kT;
   dim3 grid(nT * (nT + 1) / 2, nchunks, nw);
   k_chi0_fp64<<<grid, 256, 0, s>>>(R, w, nt, ng, nw, kchunk, part);
+  return cudaGetLastError();
+}
+
+// chi[iw] = H[v] (imaginary-axis frequency) or H[vr] + i H[vi] (real axis)
+__global__ void k_combine_freq(const double2* __restrict__ H, const int* __restrict__ vr,
+                               const int* __restrict__ vi, int64_t n2, double2* __restrict__ chi) {
+  const int iw = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n2) return;
+  const double2 a = H[(size_t)vr[iw] * n2 + e];
+  double2 v = a;
+  if (vi[iw] >= 0) {
+    const double2 b = H[(size_t)vi[iw] * n2 + e];
+    v = make_double2(a.x - b.y, a.y + b.x);
+  }
+  chi[(size_t)iw * n2 + e] = v;
+}
+
+cudaError_t launch_combine_freq(const double2* H, const int* vr, const int* vi, int ng, int nw, double2* chi,
+                                cudaStream_t s) {
+  const int64_t n2 = (int64_t)ng * ng;
+  k_combine_freq<<<dim3((unsigned)((n2 + 255) / 256), (unsigned)nw), 256, 0, s>>>(H, vr, vi, n2, chi);
   return cudaGetLastError();
 }
 

@@ -53,6 +53,14 @@ struct chi0_ctx {
   const float* term_params = nullptr;  // device parameters; NULL = off
   int term_bf16 = 1;
   DevBuf d_termx, d_termy, d_termq, d_termw, d_termc;
+  // Frequency list of the contraction: an imaginary-axis frequency is one
+  // entry (real weights); a real-axis one two, the real and imaginary parts of
+  // its complex weights, combined afterwards into chi0 = H_r + i H_i.
+  int nwv = 0;
+  bool has_real = false;
+  std::vector<double> h_vval;            // [nwv] frequency value (imaginary part, or the real frequency)
+  std::vector<int> h_vkind, h_vr, h_vi;  // [nwv] kind 0/1/2; [nw] entries of frequency iw (vi < 0: none)
+  DevBuf d_vkind, d_vr, d_vi, d_chiv;
   // Bruneval-Gonze extrapolar correction (bgterm.cu, plan in chi0_api.cu)
   int bg_on = 0;
   double bg_eps = 0.0;                 // extrapolar energy (Ha)

@@ -62,7 +62,7 @@ __global__ void k_build_eps(const double2* __restrict__ chi, const double* __res
 // P = inverse of the nb x nb pivot block (scalar Gauss-Jordan in shared memory).
 __global__ void __launch_bounds__(128)
 k_gj_pivot(double2* __restrict__ A, int ng, int b0, int nb, double2* __restrict__ pinv,
-           int* __restrict__ err) {
+           int* __restrict__ err, int general) {
   __shared__ double2 P[kNB][kNB + 1];
   const int iw = blockIdx.x;
   const double2* Am = A + (size_t)iw * ng * ng;
@@ -83,7 +83,7 @@ k_gj_pivot(double2* __restrict__ A, int ng, int b0, int nb, double2* __restrict_
       // Hermitian positive definite => real positive pivots
       const double2 d = P[p][p];
       const double mag = d.x * d.x + d.y * d.y;
-      if (!(d.x > 0.0 && mag > 1e-300)) bad = 1;
+      if (!((general || d.x > 0.0) && mag > 1e-300)) bad = 1;
       else dinv = make_double2(d.x / mag, -d.y / mag);  // 1/d
     }
     __syncthreads();
@@ -135,7 +135,7 @@ constexpr int kPE = 4;
 
 __global__ void __launch_bounds__(128)
 k_gj_panels(const double2* __restrict__ A, int ng, int b0, int nb, const double2* __restrict__ pinv,
-            double2* __restrict__ colp, double2* __restrict__ rowp) {
+            double2* __restrict__ colp, double2* __restrict__ rowp, int full) {
   __shared__ double2 base[kPE][kNB];  // A_b0+l,e of the block's columns
   const int iw = blockIdx.y;
   const double2* Am = A + (size_t)iw * ng * ng;
@@ -147,14 +147,14 @@ k_gj_panels(const double2* __restrict__ A, int ng, int b0, int nb, const double2
   const bool live = e < ng && k < nb;
   if (live) {
     double2 v;
-    if (e >= b0) {
+    if (full || e >= b0) {
       v = Am[(size_t)e * ng + b0 + k];
     } else {
       const double2 u = Am[(size_t)(b0 + k) * ng + e];
       v = make_double2(-u.x, u.y);
     }
     cp[(size_t)e * kNB + k] = v;
-    base[jj][k] = (e < b0 + nb) ? Am[(size_t)(b0 + k) * ng + e] : make_double2(v.x, -v.y);
+    base[jj][k] = (full || e < b0 + nb) ? Am[(size_t)(b0 + k) * ng + e] : make_double2(v.x, -v.y);
   }
   __syncthreads();
   if (!live) return;
@@ -175,18 +175,24 @@ constexpr int kKH = kNB / 2;
 
 __global__ void __launch_bounds__(128, 8)
 k_gj_update(double2* __restrict__ A, int ng, int b0, int nb, const double2* __restrict__ pinv,
-            const double2* __restrict__ colp, const double2* __restrict__ rowp) {
+            const double2* __restrict__ colp, const double2* __restrict__ rowp, int full) {
   __shared__ double2 Cs[kUR][kKH + 1];  // rows i of the block, k (one half)
   __shared__ double2 Rs[kKH][kUT + 1];  // k (one half), columns j of the tile
   const int iw = blockIdx.y;
   int I, J;  // lower tile: I >= J
   {
     const int t = blockIdx.x >> 1;
-    int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((r + 1) * (r + 2) / 2 <= t) ++r;
-    while (r * (r + 1) / 2 > t) --r;
-    I = r;
-    J = t - r * (r + 1) / 2;
+    if (full) {  // every tile (general matrices)
+      const int nT = (ng + kUT - 1) / kUT;
+      I = t / nT;
+      J = t - I * nT;
+    } else {     // tiles on and below the diagonal (Hermitian sweep rule)
+      int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((r + 1) * (r + 2) / 2 <= t) ++r;
+      while (r * (r + 1) / 2 > t) --r;
+      I = r;
+      J = t - r * (r + 1) / 2;
+    }
   }
   const int i0 = I * kUT + (blockIdx.x & 1) * kUR, j0 = J * kUT;
   if (i0 >= ng) return;  // the whole block lies below the matrix
@@ -289,14 +295,38 @@ cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw
   const int nt = (ng + kUT - 1) / kUT;
   for (int b0 = 0; b0 < ng; b0 += kNB) {
     const int nb = min(kNB, ng - b0);
-    k_gj_pivot<<<nw, 128, 0, s>>>(A, ng, b0, nb, pinv, err);
-    k_gj_panels<<<dim3((ng + kPE - 1) / kPE, nw), kPE * kNB, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp);
-    k_gj_update<<<dim3(nt * (nt + 1), nw), 128, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp);
+    k_gj_pivot<<<nw, 128, 0, s>>>(A, ng, b0, nb, pinv, err, 0);
+    k_gj_panels<<<dim3((ng + kPE - 1) / kPE, nw), kPE * kNB, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp, 0);
+    k_gj_update<<<dim3(nt * (nt + 1), nw), 128, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp, 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   k_gj_mirror<<<dim3((unsigned)(((int64_t)ng * ng + 255) / 256), nw), 256, 0, s>>>(A, ng);
   return cudaGetLastError();
+}
+
+// General (non-Hermitian) eps~ of real-axis frequencies: the same blocked
+// Gauss-Jordan over every tile, reading A directly, with no mirror pass.
+// Pivoting is not needed there: for w > 0 with eta > 0 every weight's
+// imaginary part is <= 0, so eps~ has a positive semidefinite imaginary
+// (anti-Hermitian) part, which every Schur complement inherits; a pivot that
+// vanishes all the same is reported through the error flag.
+cudaError_t launch_dyson_general(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,
+                                 double2* colp, double2* rowp, double2* pinv, int* err, cudaStream_t s) {
+  const int64_t n = (int64_t)ng * ng * nw;
+  k_build_eps<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(chi, vsqrt, ng, nw, A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nt = (ng + kUT - 1) / kUT;
+  for (int b0 = 0; b0 < ng; b0 += kNB) {
+    const int nb = min(kNB, ng - b0);
+    k_gj_pivot<<<nw, 128, 0, s>>>(A, ng, b0, nb, pinv, err, 1);
+    k_gj_panels<<<dim3((ng + kPE - 1) / kPE, nw), kPE * kNB, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp, 1);
+    k_gj_update<<<dim3(2 * nt * nt, nw), 128, 0, s>>>(A, ng, b0, nb, pinv, colp, rowp, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace chi0

@@ -93,10 +93,17 @@ cudaError_t launch_rho_batch(const RhoTask<T, TOUT>* tasks_dev, int ntasks, int6
 // With bg != 0 each weight is reduced by the extrapolar weight of its m
 // (a transition from m into an empty state at eps_bar): the closure form of
 // the Bruneval-Gonze correction.
+// omega_im[iw] and vkind[iw] (NULL: all kind 0) describe the contraction's
+// frequency list: kind 0 an imaginary-axis frequency i omega_im (real
+// weights); kinds 1 and 2 the real and imaginary parts of the complex weights
+// at the real frequency omega_im.
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
                            const double* eps, const double* occ, const double* omega_im,
-                           const double* omega_re, int nw, double eta, double pref,
+                           const int* vkind, int nw, double eta, double pref,
                            double occ_tol, int bg, double eps_bar, double* w, cudaStream_t s);
+// chi[iw] = H[vr[iw]] + i H[vi[iw]] (vi[iw] < 0: chi[iw] = H[vr[iw]])
+cudaError_t launch_combine_freq(const double2* H, const int* vr, const int* vi, int ng, int nw, double2* chi,
+                                cudaStream_t s);
 
 // Bruneval-Gonze correction, the two steps after the contraction:
 // P[iw][d] = sum_t wbar[iw][t] rd(t, d) over the diagonal densities rd of the
@@ -135,6 +142,10 @@ cudaError_t launch_chi0_reduce(const double2* part, int nchunks, int ng, int nw,
 cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,
                          double2* colpanel, double2* rowpanel, double2* pinv, int* err_flag,
                          cudaStream_t s);
+// The same for general eps~ (real-axis frequencies): every tile, no symmetry.
+cudaError_t launch_dyson_general(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,
+                                 double2* colpanel, double2* rowpanel, double2* pinv, int* err_flag,
+                                 cudaStream_t s);
 // The Dyson kernels prefer the whole shared-memory carveout, the setting of
 // the tensor-core contraction, so that both can share an SM.
 cudaError_t dyson_prepare();
