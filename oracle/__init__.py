@@ -18,7 +18,9 @@ theory calculations using the yambo code", J. Phys.: Condens. Matter 31,
 * the bare Coulomb interaction v(q+G) = 4 pi / |q+G|^2 of the Coulomb
   interaction subsection and the symmetric form of Eq. (W_def);
 * the Bruneval-Gonze extrapolar correction of Eq. (X_term_def) and
-  Appendix C through the closure relation over the bands at k.
+  Appendix C through the closure relation over the bands at k;
+* the Godby-Needs plasmon-pole fit of eps^-1 at w = 0 and w = i w_p (Full
+  frequency GW subsection).
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 against invariants, closed forms or independent routes.
@@ -34,3 +36,4 @@ from .chi0 import (  # noqa: F401
 )
 from .dyson import eps_tilde, eps_inv_gauss_jordan, eps_inv_rpa_route  # noqa: F401
 from .bg_terminator import diag_density, extrapolar_weights, delta_chi_bg, chi0_bg  # noqa: F401
+from .ppa import ppa_fit, ppa_eval  # noqa: F401
