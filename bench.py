@@ -120,10 +120,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def build_system(kgrid=None, nw=32, real_axis=False):
+PPA_OMEGA_P = 1.0          # Ha: the plasmon-pole model's second fit point i omega_p (PPAPntXp default)
+PPA_ETA_EV = 0.1           # broadening of the model's real-axis evaluation
+
+
+def ppa_real_freqs(n):
+    from synth import HA_EV
+    return np.arange(1, n + 1) * (100.0 / n) / HA_EV + 0j
+
+
+def build_system(kgrid=None, nw=32, real_axis=False, ppa=False):
     """The precision workload; kgrid / nw override it for smaller profiling
     runs; real_axis puts its nw frequencies on the real axis instead (evenly
-    spaced on (0, 100] eV, broadening 0.1 eV)."""
+    spaced on (0, 100] eV, broadening 0.1 eV); ppa keeps only the plasmon-pole
+    fit points w = 0 and w = i omega_p."""
     import dataclasses
     from synth import HA_EV, cfg_precision, make_system
     spec = cfg_precision(nw=nw)
@@ -132,6 +142,8 @@ def build_system(kgrid=None, nw=32, real_axis=False):
     if real_axis:
         w = np.arange(1, nw + 1) * (100.0 / nw) / HA_EV
         spec = dataclasses.replace(spec, freqs=tuple(complex(x, 0.0) for x in w), eta=0.1 / HA_EV)
+    if ppa:
+        spec = dataclasses.replace(spec, freqs=(0j, 1j * PPA_OMEGA_P))
     return make_system(spec)
 
 
@@ -139,6 +151,10 @@ def workload_name(args):
     base = _workload_base(args)
     if getattr(args, "real_axis", False):
         base = base.replace(" imaginary GL frequencies in [0,100] eV", " real frequencies on (0,100] eV, eta 0.1 eV")
+    if getattr(args, "ppa", None):
+        base = base.replace(f"{args.nw} imaginary GL frequencies in [0,100] eV",
+                            f"chi0 and eps^-1 at w = 0 and i 1 Ha, Godby-Needs plasmon-pole fit, "
+                            f"model on {args.ppa} real frequencies on (0,100] eV, eta 0.1 eV")
     if getattr(args, "bg_terminator", None) is not None:
         base += f", Bruneval-Gonze extrapolar correction at {args.bg_terminator:g} eV"
     return base
@@ -211,7 +227,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    s = build_system(args.kgrid, args.nw, args.real_axis)
+    s = build_system(args.kgrid, args.nw, args.real_axis, ppa=bool(args.ppa))
     ng, nw = s.ng, s.freqs.size
     prec = lib.CHI0_MIXED_BF16X3 if args.precision == "mixed" else lib.CHI0_FP64
     ctx = lib.Chi0.for_system(s, precision=prec, stream=stream.cuda_stream)
@@ -225,10 +241,37 @@ def run_ours(args, rank, world, dist):
         from synth import HA_EV
         ctx.set_bg_terminator(args.bg_terminator / HA_EV)
     inv_d = torch.empty((nw, ng, ng), dtype=torch.complex128, device=dev)
+    ppa_ms = [0.0, 0.0]
+    ppa_launches = 0
+    if args.ppa:
+        from synth import HA_EV
+        ppa_w = ppa_real_freqs(args.ppa)
+        ppa_eta = PPA_ETA_EV / HA_EV
+        wt_d = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
+        pr_d = torch.empty_like(wt_d)
+        model_d = torch.empty((args.ppa, ng, ng), dtype=torch.complex128, device=dev)
+        # one event triple per timed step, read after the timed region
+        ppa_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
 
-    def step():
+    ppa_done = []
+
+    def ppa_step(timed):
+        ev = ppa_ev[len(ppa_done)] if timed else None
+        if ev:
+            ev[0].record(stream)
+        lib.ppa_fit(inv_d[0], inv_d[1], PPA_OMEGA_P, wt_d, pr_d, stream.cuda_stream)
+        if ev:
+            ev[1].record(stream)
+        lib.ppa_eval(wt_d, pr_d, ppa_w, ppa_eta, model_d, stream.cuda_stream)
+        if ev:
+            ev[2].record(stream)
+            ppa_done.append(ev)
+
+    def step(timed=False):
         ctx.compute_rho(0)
         ctx.build_invert(0, inv_d)
+        if args.ppa:
+            ppa_step(timed)
 
     for _ in range(args.warmup):
         step()
@@ -248,14 +291,18 @@ def run_ours(args, rank, world, dist):
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            step()
+            step(timed=True)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
+    for a, b, c in ppa_done:
+        ppa_ms[0] += a.elapsed_time(b)
+        ppa_ms[1] += b.elapsed_time(c)
+        ppa_launches += 1 + -(-args.ppa // 32)
     ms_total = ev0.elapsed_time(ev1)
     ctx.synchronize()
     st_ms, st_bytes, st_flops, l1 = ctx.get_stats()
-    launches = (l1 - l0)
+    launches = (l1 - l0) + ppa_launches
     if dist is not None:
         t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -267,7 +314,7 @@ def run_ours(args, rank, world, dist):
     # ---- end to end: host buffers, copies inside the timed region
     pin_gv = [torch.from_numpy(np.ascontiguousarray(s.gvec[ik, :s.npw[ik]])).pin_memory() for ik in range(s.nk)]
     pin_cf = [torch.from_numpy(np.ascontiguousarray(s.coef[ik, :, :s.npw[ik]])).pin_memory() for ik in range(s.nk)]
-    out_h = torch.empty((nw, ng, ng), dtype=torch.complex128).pin_memory()
+    out_h = torch.empty((args.ppa or nw, ng, ng), dtype=torch.complex128).pin_memory()
     h2d = sum(int(x.numel() * x.element_size()) for x in pin_gv + pin_cf) + 2 * s.eps.nbytes
     d2h = int(out_h.numel() * out_h.element_size())
 
@@ -276,7 +323,12 @@ def run_ours(args, rank, world, dist):
             ctx.set_wavefunctions(ik, pin_gv[ik], pin_cf[ik])
         ctx.set_energies(s.eps, s.occ)
         ctx.compute_rho(0)
-        ctx.build_invert(0, out_h)   # device -> host copy of the result, synchronises
+        if args.ppa:
+            ctx.build_invert(0, inv_d)
+            ppa_step(False)
+            out_h.copy_(model_d)     # the model on the real axis, device -> host
+        else:
+            ctx.build_invert(0, out_h)   # device -> host copy of the result, synchronises
 
     if args.no_e2e:
         e2e_ms = None
@@ -339,6 +391,22 @@ def run_ours(args, rank, world, dist):
     if tsrc:
         roof["traffic_source"] = tsrc
     roof.update(extra)
+    ppa_line = None
+    if args.ppa:
+        n2 = ng * ng
+        fit_bytes = 64.0 * n2
+        eval_bytes = (32.0 * -(-args.ppa // 32) + 16.0 * args.ppa) * n2
+        fit_ms, eval_ms = ppa_ms[0] / args.steps, ppa_ms[1] / args.steps
+        ppa_line = {"omega_p_ha": PPA_OMEGA_P, "n_real_freqs": args.ppa, "fit_ms": fit_ms, "eval_ms": eval_ms,
+                    "fit_gbs": fit_bytes / (fit_ms * 1e-3) / 1e9, "eval_gbs": eval_bytes / (eval_ms * 1e-3) / 1e9,
+                    "fit_hbm_frac": fit_bytes / (fit_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                    "eval_hbm_frac": eval_bytes / (eval_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                    "bytes_per_element": {"fit": 64, "eval": eval_bytes / n2},
+                    # the evaluation is bound by the FP64 units: 20 FP64 operations per
+                    # element and frequency (the reciprocal counted as one)
+                    "eval_fp64_tflops": 20.0 * n2 * args.ppa / (eval_ms * 1e-3) / 1e12,
+                    "eval_fp64_frac": 20.0 * n2 * args.ppa / (eval_ms * 1e-3) / 1e12 / FP64_PEAK,
+                    "fp64_peak_source": FP64_SRC}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -353,6 +421,8 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if ppa_line is not None:
+        line["ppa"] = ppa_line
     if not args.no_cpu_baseline:
         import oracle as O
         G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
@@ -384,7 +454,12 @@ def main():
                          "general Dyson step)")
     ap.add_argument("--bg-terminator", type=float, default=None, metavar="EV",
                     help="apply the Bruneval-Gonze extrapolar correction with this extrapolar energy (eV)")
+    ap.add_argument("--ppa", type=int, default=0, metavar="NW",
+                    help="plasmon-pole path: chi0 and eps^-1 at w = 0 and i 1 Ha only, the Godby-Needs fit and "
+                         "the model on NW real frequencies on (0, 100] eV")
     args = ap.parse_args()
+    if args.ppa and (args.real_axis or args.ppa < 0):
+        ap.error("--ppa takes a positive count and excludes --real-axis")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

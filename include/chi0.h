@@ -337,6 +337,35 @@ chi0_status chi0_set_terminator(chi0_ctx* ctx, const float* params, int bf16);
  * Errors: CHI0_EINVAL (eps_bar not finite, learned terminator set). */
 chi0_status chi0_set_bg_terminator(chi0_ctx* ctx, int on, double eps_bar);
 
+/* ---- Godby-Needs plasmon-pole model ------------------------------------------
+ * Full frequency GW subsection: eps^-1_GG'(w) is modelled by one pole pair per
+ * element, its two parameters chosen so that the model reproduces eps^-1 at
+ * w = 0 and at w = i omega_p (PPAPntXp, default 1 Ha).  With
+ * x(w) = eps^-1_GG'(w) - delta_GG' the model is, in the retarded form of the
+ * chi0 weights,
+ *   x(w) = R [1/(w - wt + i eta) - 1/(w + wt + i eta)],
+ * so that wt^2 = omega_p^2 x(i omega_p) / (x(0) - x(i omega_p)) and
+ * R = -x(0) wt / 2 (wt the principal square root).  An element with
+ * Re wt^2 <= 0, or with x(0) = x(i omega_p), has no real pole and keeps its
+ * static value: wt = 0 and R = x(0) mark it.
+ * All matrices are device pointers, [ng][ng] complex128 (row-major, the
+ * layout of chi0_invert_eps's output for one frequency), owned by the caller;
+ * the calls are asynchronous on cuda_stream (NULL = default stream) and
+ * allocate nothing.
+ * Errors: CHI0_EINVAL (NULL pointer, ng < 1, omega_p not finite and > 0),
+ * CHI0_ECUDA. */
+chi0_status chi0_ppa_fit(const void* eps_inv_0, const void* eps_inv_p, int ng, double omega_p,
+                         void* omega_t, void* R, void* cuda_stream);
+
+/* eps^-1 of the model at nf complex frequencies: freqs is a host array of nf
+ * (re, im) pairs (copied; may be NULL when nf = 0), eta >= 0 the broadening,
+ * out a device pointer to [nf][ng][ng] complex128.  A frequency on a pole
+ * (w + i eta = +-wt exactly) gives an infinite entry.  Errors: CHI0_EINVAL
+ * (NULL pointer, ng < 1, nf < 0, eta or a frequency not finite, eta < 0),
+ * CHI0_ECUDA. */
+chi0_status chi0_ppa_eval(const void* omega_t, const void* R, int ng, const double* freqs, int nf,
+                          double eta, void* out, void* cuda_stream);
+
 /* Text of the last error on ctx (static storage inside ctx; never NULL). */
 const char* chi0_last_error(const chi0_ctx* ctx);
 

@@ -30,6 +30,7 @@ EXPORTS = (
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator", "chi0_set_bg_terminator",
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
+    "chi0_ppa_fit", "chi0_ppa_eval",
 )
 
 
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_batch_run.argtypes = [P, P]
     lib.chi0_batch_rho_width.argtypes = [P]
     lib.chi0_batch_destroy.argtypes = [P]
+    lib.chi0_ppa_fit.argtypes = [P, P, I, D, P, P, P]
+    lib.chi0_ppa_eval.argtypes = [P, P, I, P, I, D, P, P]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy", "chi0_batch_destroy"):
             getattr(lib, name).restype = I
@@ -135,6 +138,28 @@ def invert_eps_noalloc(chi0, v_sqrt, out, stream=None):
     if st != 0:
         raise Chi0Error(st, "chi0_invert_eps_noalloc failed")
     return out
+
+
+def ppa_fit(eps_inv_0, eps_inv_p, omega_p, omega_t, R, stream=None):
+    """chi0_ppa_fit: plasmon-pole parameters (omega_t, R) of every element from
+    eps^-1 at w = 0 and w = i omega_p.  All four are contiguous complex128
+    CUDA tensors [ng][ng]."""
+    ng = int(eps_inv_0.shape[-1])
+    st = _lib.chi0_ppa_fit(_dev(eps_inv_0), _dev(eps_inv_p), ng, float(omega_p), _dev(omega_t), _dev(R), stream)
+    if st != 0:
+        raise Chi0Error(st, "chi0_ppa_fit failed")
+
+
+def ppa_eval(omega_t, R, freqs, eta, out, stream=None):
+    """chi0_ppa_eval: eps^-1 of the plasmon-pole model at the complex
+    frequencies freqs (host) into out, a complex128 CUDA tensor [nf][ng][ng]."""
+    f = np.ascontiguousarray(np.asarray(freqs, dtype=np.complex128).reshape(-1))
+    fr = np.ascontiguousarray(np.stack([f.real, f.imag], axis=1).reshape(-1))
+    ng = int(omega_t.shape[-1])
+    st = _lib.chi0_ppa_eval(_dev(omega_t), _dev(R), ng, fr.ctypes.data if f.size else None, int(f.size),
+                            float(eta), _dev(out), stream)
+    if st != 0:
+        raise Chi0Error(st, "chi0_ppa_eval failed")
 
 
 class Batch:
