@@ -622,7 +622,7 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
 }
 
 // kernels of build_chi0 (weights, contraction, reduction, terminator)
-chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep) {
+chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep, bool defer_combine) {
   const int iq = c->plan_chi_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "chi0 not planned");
   const int nw0 = c->cfg.nw, nw = c->nwv, ng = c->cfg.ng;
@@ -674,7 +674,7 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
                           c->bg_on ? &bga : nullptr);
       if (s != CHI0_OK) return s;
     }
-    if (c->has_real) {
+    if (c->has_real && !defer_combine) {
       chi0::stage_begin(c, CHI0_STAGE_REDUCE);
       e = chi0::launch_combine_freq(chiv, (const int*)c->d_vr.p, (const int*)c->d_vi.p, ng, nw0,
                                     (double2*)c->d_chi.p, c->st);
@@ -727,7 +727,8 @@ chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
     cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join_ct, &c->ev_join_dy};
     for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "pipeline event");
   }
-  while ((int)c->ev_freq.size() < nw) {
+  // one event per entry of the contraction's frequency list
+  while ((int)c->ev_freq.size() < std::max(nw, c->nwv)) {
     cudaEvent_t e = nullptr, f = nullptr;
     CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "pipeline event");
     c->ev_freq.push_back(e);
@@ -778,7 +779,7 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
   if (iq < 0 || c->plan_eps_iq != iq) return fail(c, CHI0_ESTATE, "build and Dyson step not planned");
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   chi0_status s;
-  if (c->fp64 || c->term_params || c->has_real || c->nt == 0 || nw < 2) {
+  if (c->fp64 || c->term_params || c->nt == 0 || nw < 2) {
     // FP64 contraction and Dyson share the FP64 pipe; the learned terminator
     // needs every frequency of chi0 first: no overlap to gain
     if ((s = launch_chi0(c)) != CHI0_OK) return s;
@@ -790,29 +791,52 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
   cudaStreamWaitEvent(c->s_ct, c->ev_fork, 0);
   cudaStreamWaitEvent(c->s_dy, c->ev_fork, 0);
   c->st = c->s_ct;
-  s = launch_chi0(c, c->ev_freq.data(), c->ev_prep.data());
+  s = launch_chi0(c, c->ev_freq.data(), c->ev_prep.data(), /*defer_combine=*/true);
   c->st = c->s_dy;
   // Dyson steps in groups of 4 frequencies: the pivot-block inverses of a
   // group run side by side (one SM each), which a single frequency's chain
   // of 32 dependent pivot steps cannot hide.  The last four frequencies go
   // as 2, 1, 1, so that after the last contraction only one frequency's
-  // Dyson step is left.
+  // Dyson step is left.  A group holds frequencies of one kind (imaginary
+  // axis: Hermitian eps~; real axis: general eps~, whose chi0 is first
+  // combined from its two contractions H_r + i H_i).
   const int nT = (ng + 31) / 32;
+  auto general = [&](int iw) { return c->has_real && c->h_vi[iw] >= 0; };
+  auto first_v = [&](int iw) { return c->has_real ? c->h_vr[iw] : iw; };   // list entries of frequency iw
+  auto last_v = [&](int iw) { return general(iw) ? c->h_vi[iw] : first_v(iw); };
   for (int w0 = 0; w0 < nw && s == CHI0_OK;) {
     const int r = nw - w0;
-    const int gw = r > 4 ? std::min(4, r - 4) : (r == 4 ? 2 : 1);
-    cudaStreamWaitEvent(c->s_dy, c->ev_freq[w0 + gw - 1], 0);
+    int gw = r > 4 ? std::min(4, r - 4) : (r == 4 ? 2 : 1);
+    for (int g = 1; g < gw; ++g)
+      if (general(w0 + g) != general(w0)) {
+        gw = g;
+        break;
+      }
+    cudaStreamWaitEvent(c->s_dy, c->ev_freq[last_v(w0 + gw - 1)], 0);
     // and, when a split pass follows, until it is done: the Dyson blocks then
     // share the SMs with the (tensor-bound) contraction, not with the
     // (bandwidth-bound) split
-    if (w0 + gw < nw) cudaStreamWaitEvent(c->s_dy, c->ev_prep[w0 + gw], 0);
+    if (w0 + gw < nw) cudaStreamWaitEvent(c->s_dy, c->ev_prep[first_v(w0 + gw)], 0);
+    cudaError_t e = cudaSuccess;
+    if (c->has_real) {
+      chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+      e = chi0::launch_combine_freq((const double2*)c->d_chiv.p, (const int*)c->d_vr.p + w0,
+                                    (const int*)c->d_vi.p + w0, ng, gw, (double2*)c->d_chi.p + w0 * n2, c->s_dy);
+      chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+      if (e != cudaSuccess) s = cuda_fail(c, e, "frequency combine launch");
+    }
+    if (s != CHI0_OK) break;
     chi0::stage_begin(c, CHI0_STAGE_DYSON);
-    cudaError_t e = chi0::launch_dyson((const double2*)c->d_chi.p + w0 * n2, (const double*)c->d_vsqrt.p,
-                                       ng, gw, c->plan_eps_out + w0 * n2, (double2*)c->d_colp.p,
-                                       (double2*)c->d_rowp.p, (double2*)c->d_pinv.p, (int*)c->d_err.p,
-                                       c->s_dy);
+    const double2* chi = (const double2*)c->d_chi.p + w0 * n2;
+    double2* out = c->plan_eps_out + w0 * n2;
+    e = general(w0) ? chi0::launch_dyson_general(chi, (const double*)c->d_vsqrt.p, ng, gw, out,
+                                                 (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
+                                                 (double2*)c->d_pinv.p, (int*)c->d_err.p, c->s_dy)
+                    : chi0::launch_dyson(chi, (const double*)c->d_vsqrt.p, ng, gw, out, (double2*)c->d_colp.p,
+                                         (double2*)c->d_rowp.p, (double2*)c->d_pinv.p, (int*)c->d_err.p,
+                                         c->s_dy);
     if (e != cudaSuccess) s = cuda_fail(c, e, "dyson launch");
-    chi0::stage_end(c, CHI0_STAGE_DYSON, 2 + 3 * nT);
+    chi0::stage_end(c, CHI0_STAGE_DYSON, (general(w0) ? 1 : 2) + 3 * nT);
     w0 += gw;
   }
   c->st = base;

@@ -121,8 +121,10 @@ chi0_status term_launch(chi0_ctx* c, double2* chi);
 chi0_status plan_rho(chi0_ctx* c, int iq);
 chi0_status launch_rho(chi0_ctx* c, bool with_pairs);
 chi0_status plan_chi0(chi0_ctx* c, int iq);
+// defer_combine leaves the real-axis frequencies as their parts H_r, H_i
+// (the caller combines them, frequency group by group)
 chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq = nullptr,
-                        const cudaEvent_t* ev_prep = nullptr);
+                        const cudaEvent_t* ev_prep = nullptr, bool defer_combine = false);
 chi0_status plan_eps(chi0_ctx* c, int iq, double2* A);
 chi0_status launch_eps(chi0_ctx* c);
 // build_chi0 and invert_eps as one pipeline: the Dyson step of frequency w

@@ -98,7 +98,9 @@ def test_real_axis_build_invert_and_batch(lib):
     ctx.compute_rho(0)
     ctx.build_invert(0, inv_b, chi_b)
     ctx.synchronize()
-    assert torch.equal(chi_a, chi_b) and torch.equal(inv_a, inv_b)
+    # build_invert runs the Dyson step in frequency groups beside the contraction
+    assert torch.equal(chi_a, chi_b)
+    assert (inv_b - inv_a).abs().max().item() <= 1e-13 * inv_a.abs().max().item()
     out = torch.zeros_like(chi_a)
     batch = lib.Batch([ctx], [0], [out], nstreams=1)
     batch.run(stream)
