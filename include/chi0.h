@@ -337,6 +337,35 @@ chi0_status chi0_set_terminator(chi0_ctx* ctx, const float* params, int bf16);
  * Errors: CHI0_EINVAL (eps_bar not finite, learned terminator set). */
 chi0_status chi0_set_bg_terminator(chi0_ctx* ctx, int on, double eps_bar);
 
+/* ---- Self-energy kernel I (full-frequency GW) --------------------------------
+ * Full frequency GW subsection, Eqs. (W_def), (W_delta), (I_c):
+ *   I^{ab k}_{m q}(w) = -1/(N_k Omega) sum_{G,G'} W^d_GG'(q,w) rho_{amk}(q,G) conj(rho_{bmk}(q,G')),
+ * W = V eps~^-1 V (Eq. W_def in the symmetric form, V_i = sqrt(4 pi)/|q+G_i|),
+ *   W^d_GG' = 1/2 Im(W_GG' + W_G'G) - i/2 Re(W_GG' - W_G'G)   (Eq. W_delta),
+ * a, b bands of the quasiparticle window [qp_lo, qp_hi) at k, m every band
+ * (0 .. nbands-1) at k - q, rho of Eq. (rhotw) as for chi0, for every k of
+ * the grid.  W^d vanishes where eps~^-1 is Hermitian (imaginary axis); it is
+ * the spectral part of W on the real axis.
+ *   eps_inv: DEVICE pointer, [nw][ng][ng] complex128: eps~^-1 of the response
+ *            set of q index iq at nw frequencies (as written by
+ *            chi0_invert_eps / chi0_build_invert with out_on_device = 1, or
+ *            by chi0_ppa_eval); read only.
+ *   out:     [nw][nk][nbands][nqp][nqp] complex128, nqp = qp_hi - qp_lo,
+ *            entry [w][k][m][a - qp_lo][b - qp_lo]; device (out_on_device = 1,
+ *            asynchronous on the context's stream) or host (synchronises).
+ * The contraction sum_j W^d_ij conj(rho(j)) runs on the tensor cores in the
+ * mixed form (BF16x3 products, FP32 accumulation in 128-term pieces, FP64
+ * sums), in plain FP64 in the FP64 form.  Requires chi0_compute_rho(iq)
+ * (mixed-grid wavefunctions and the response set).  Device memory: rho of
+ * the window (nk nbands nqp ng complex) and an N_G x nk nbands nqp FP64
+ * complex work array.
+ * Errors: CHI0_EINVAL (window empty or outside [0, nbands), NULL pointer,
+ * nw < 1, |q+G| = 0), CHI0_EUNSUPPORTED (more than 64 bands in the window,
+ * or too many transitions for one contraction), CHI0_ESTATE, CHI0_ENOMEM,
+ * CHI0_ECUDA, CHI0_ETIMEOUT. */
+chi0_status chi0_build_sigma_i(chi0_ctx* ctx, int iq, int qp_lo, int qp_hi, const void* eps_inv, int nw,
+                               void* out, int out_on_device);
+
 /* ---- Godby-Needs plasmon-pole model ------------------------------------------
  * Full frequency GW subsection: eps^-1_GG'(w) is modelled by one pole pair per
  * element, its two parameters chosen so that the model reproduces eps^-1 at

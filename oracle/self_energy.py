@@ -38,21 +38,21 @@ def w_delta(W):
     return 0.5 * (W.imag + Wt.imag) - 0.5j * (W.real - Wt.real)
 
 
-def i_kernel(system, iq, Gs, qp_bands, Wd, ks=None):
+def i_kernel(system, iq, Gs, qp_bands, Wd, ks=None, ms=None):
     """I[k, m, a, b] = I^{n_a n_b k}_{m q} of Eq. (I_c) for one frequency.
 
-    qp_bands: the band indices n at k (n_a, n_b run over them); m runs over
-    every band at k - q; ks: the k indices (default all).  Wd: W^delta on the
-    G vectors Gs (N_G x N_G)."""
+    qp_bands: the band indices n at k (n_a, n_b run over them); ks: the k
+    indices (default all); ms: the bands m at k - q (default all).  Wd:
+    W^delta on the G vectors Gs (N_G x N_G)."""
     ks = range(system.nk) if ks is None else ks
     qp_bands = np.asarray(qp_bands, dtype=np.int64)
-    all_m = np.arange(system.nb)
+    ms = np.arange(system.nb) if ms is None else np.asarray(ms, dtype=np.int64)
     Wd = np.asarray(Wd, dtype=np.complex128)
     pref = -1.0 / (system.nk * system.omega_cell)
-    out = np.zeros((len(ks), system.nb, qp_bands.size, qp_bands.size), dtype=np.complex128)
+    out = np.zeros((len(ks), ms.size, qp_bands.size, qp_bands.size), dtype=np.complex128)
     for j, ik in enumerate(ks):
-        rho = rho_block(system, iq, Gs, int(ik), qp_bands, all_m, shifted=True)   # [n, m, G]
-        for m in range(system.nb):
-            r = rho[:, m, :]                                                      # [n, G]
-            out[j, m] = pref * (r @ Wd @ np.conj(r).T)
+        rho = rho_block(system, iq, Gs, int(ik), qp_bands, ms, shifted=True)      # [n, m, G]
+        for jm in range(ms.size):
+            r = rho[:, jm, :]                                                     # [n, G]
+            out[j, jm] = pref * (r @ Wd @ np.conj(r).T)
     return out

@@ -30,7 +30,7 @@ EXPORTS = (
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator", "chi0_set_bg_terminator",
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
-    "chi0_ppa_fit", "chi0_ppa_eval",
+    "chi0_ppa_fit", "chi0_ppa_eval", "chi0_build_sigma_i",
 )
 
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_batch_rho_width.argtypes = [P]
     lib.chi0_batch_destroy.argtypes = [P]
     lib.chi0_ppa_fit.argtypes = [P, P, I, D, P, P, P]
+    lib.chi0_build_sigma_i.argtypes = [P, I, I, I, P, I, P, I]
     lib.chi0_ppa_eval.argtypes = [P, P, I, P, I, D, P, P]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy", "chi0_batch_destroy"):
@@ -329,6 +330,15 @@ class Chi0:
     def invert_eps(self, iq, out):
         p, dev = _ptr(out)
         self._check(_lib.chi0_invert_eps(self.h, int(iq), p, dev))
+        return out
+
+    def build_sigma_i(self, iq, qp_lo, qp_hi, eps_inv, out):
+        """chi0_build_sigma_i: the self-energy kernel I of Eq. (I_c) from eps~^-1
+        (a contiguous complex128 CUDA tensor [nw][ng][ng]) into out, numpy or a
+        tensor of shape [nw][nk][nbands][nqp][nqp] complex128."""
+        p, dev = _ptr(out)
+        self._check(_lib.chi0_build_sigma_i(self.h, int(iq), int(qp_lo), int(qp_hi), _dev(eps_inv),
+                                            int(eps_inv.shape[0]), p, dev))
         return out
 
     def build_invert(self, iq, eps_out, chi_out=None):

@@ -1095,6 +1095,121 @@ chi0_status chi0_set_bg_terminator(chi0_ctx* c, int on, double eps_bar) {
   return CHI0_OK;
 }
 
+chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const void* eps_inv, int nw,
+                               void* out, int out_on_device) {
+  if (!c) return CHI0_EINVAL;
+  if (iq < 0 || iq >= c->cfg.nq) return fail(c, CHI0_EINVAL, "iq %d out of range", iq);
+  if (qp_lo < 0 || qp_hi > c->nb || qp_hi <= qp_lo)
+    return fail(c, CHI0_EINVAL, "quasiparticle window [%d, %d) is empty or outside [0, %d)", qp_lo, qp_hi, c->nb);
+  if (!eps_inv || !out || nw < 1) return fail(c, CHI0_EINVAL, "NULL eps~^-1 or output, or nw < 1");
+  const int nqp = qp_hi - qp_lo;
+  if (nqp > 64) return fail(c, CHI0_EUNSUPPORTED, "at most 64 bands in the quasiparticle window");
+  if (iq != c->rho_iq) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
+  if (c->nt == 0)
+    return fail(c, CHI0_ESTATE, "no transitions at this q: the mixed-grid wavefunctions were not built");
+  const int ng = c->cfg.ng, nb = c->nb;
+  const int64_t T = (int64_t)c->nk * nb * nqp;
+  const size_t cb = cplx_bytes(c);
+  chi0_status s;
+  // rho geometry of the window: n in [qp_lo, qp_hi) at k, every band m at k - q
+  RhoGeom& g = c->sig_geom;
+  g = c->geom;
+  g.n_lo = qp_lo;
+  g.Nn = nqp;
+  g.Nm = nb;
+  g.diag = 0;
+  const int64_t nI = (ng + 63) / 64, nJ = (T + 63) / 64;
+  const size_t osz = (size_t)c->nk * nb * nqp * nqp * 16;   // I of one frequency
+  if ((s = ensure(c, c->d_sigR, (size_t)T * ng * cb, "quasiparticle rho")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_sigY, (size_t)nI * nJ * 4096 * 16, "W^delta rho* tiles")) != CHI0_OK) return s;
+  if (!out_on_device && (s = ensure(c, c->d_sigI, osz, "I staging")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_vsqrt, (size_t)ng * 8, "coulomb")) != CHI0_OK) return s;
+  if (c->fp64) {
+    if ((s = ensure(c, c->d_sigWd, (size_t)ng * ng * 16, "W^delta")) != CHI0_OK) return s;
+  } else if ((s = chi0::sig_tc_plan(c, T, ng)) != CHI0_OK) {
+    return s;
+  }
+  if (!c->d_err.p) {
+    if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
+    CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
+  }
+  // V_i = sqrt(4 pi) / |q + G_i| on the response set of iq
+  {
+    std::vector<double> v(ng);
+    int64_t qi[3];
+    q_integers(c, iq, qi);
+    for (int i = 0; i < ng; ++i) {
+      double q2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double comp = (double)qi[d] / c->cfg.kgrid[d] + c->h_gresp[3 * i + d];
+        q2 += comp * comp;
+      }
+      const double qg = (2.0 * M_PI / c->a) * std::sqrt(q2);
+      if (qg == 0.0) return fail(c, CHI0_EINVAL, "|q+G| = 0: bare Coulomb interaction diverges");
+      v[i] = std::sqrt(4.0 * M_PI) / qg;
+    }
+    CK(cudaMemcpyAsync(c->d_vsqrt.p, v.data(), (size_t)ng * 8, cudaMemcpyHostToDevice, c->st), "v H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  }
+  cudaError_t e;
+  chi0::stage_begin(c, CHI0_STAGE_RHO);
+  if (c->fp64)
+    e = chi0::launch_rho_pairs<double, double2>(g, (const double2*)c->d_U.p, (const int32_t*)c->d_kq.p,
+                                                (const int32_t*)c->d_g0.p, (const int32_t*)c->d_gresp.p,
+                                                (const int32_t*)c->d_gperm.p, (const double2*)c->d_tw1.p,
+                                                (const double2*)c->d_tw2.p, (double2*)c->d_sigR.p, c->st);
+  else
+    e = chi0::launch_rho_pairs<float, float2>(g, (const float2*)c->d_U.p, (const int32_t*)c->d_kq.p,
+                                              (const int32_t*)c->d_g0.p, (const int32_t*)c->d_gresp.p,
+                                              (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p,
+                                              (const float2*)c->d_tw2.p, (float2*)c->d_sigR.p, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "quasiparticle rho launch");
+  chi0::stage_end(c, CHI0_STAGE_RHO, 1);
+  if (!c->fp64) {
+    chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
+    if ((e = chi0::sig_tc_split_b(c, (const float2*)c->d_sigR.p, nqp, nb)) != cudaSuccess)
+      return cuda_fail(c, e, "rho split launch");
+    chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+  }
+  const double pref = -1.0 / ((double)c->nk * c->omega_cell);   // Eq. (I_c)
+  const size_t n2 = (size_t)ng * ng;
+  const double* v = (const double*)c->d_vsqrt.p;
+  double2* Y = (double2*)c->d_sigY.p;
+  for (int iw = 0; iw < nw; ++iw) {
+    const double2* E = (const double2*)eps_inv + iw * n2;
+    double2* I = out_on_device ? (double2*)((char*)out + iw * osz) : (double2*)c->d_sigI.p;
+    chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
+    e = c->fp64 ? chi0::launch_sig_wd64(E, v, ng, (double2*)c->d_sigWd.p, c->st) : chi0::sig_tc_split_a(c, E, v);
+    if (e != cudaSuccess) return cuda_fail(c, e, "W^delta launch");
+    chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+    chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
+    e = c->fp64 ? chi0::launch_sig_gemm64((const double2*)c->d_sigWd.p, (const double2*)c->d_sigR.p, ng, T, nqp, nb,
+                                          Y, c->st)
+                : chi0::sig_tc_contract(c, Y);
+    if (e != cudaSuccess) return cuda_fail(c, e, "W^delta rho* contraction launch");
+    chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
+    chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+    e = c->fp64 ? chi0::launch_sig_dot<double2>((const double2*)c->d_sigR.p, Y, ng, T, nqp, nb, pref, I, c->st)
+                : chi0::launch_sig_dot<float2>((const float2*)c->d_sigR.p, Y, ng, T, nqp, nb, pref, I, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "I launch");
+    chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+    if (!out_on_device)
+      CK(cudaMemcpyAsync((char*)out + iw * osz, I, osz, cudaMemcpyDeviceToHost, c->st), "I copy out");
+  }
+  // algorithmic work of the last call: rho of the window, one complex
+  // contraction of N_G^2 T multiply-adds and one of N_G T nqp per frequency
+  c->stage[CHI0_STAGE_RHO].bytes = (double)T * ng * cb;
+  c->stage[CHI0_STAGE_CONTRACT].flops = 8.0 * (double)ng * ng * (double)T * nw;
+  c->stage[CHI0_STAGE_CONTRACT].bytes = ((double)ng * ng * 16 + (double)T * ng * cb + (double)T * ng * 16) * nw;
+  c->stage[CHI0_STAGE_REDUCE].flops = 8.0 * (double)ng * (double)T * nqp * nw;
+  c->stage[CHI0_STAGE_REDUCE].bytes = ((double)T * ng * 16 + (double)osz) * nw;
+  if (!out_on_device) {
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+    return check_device_error(c);
+  }
+  return CHI0_OK;
+}
+
 chi0_status chi0_get_response_gvectors(chi0_ctx* c, int iq, int32_t* out) {
   if (!c) return CHI0_EINVAL;
   if (iq < 0 || iq >= c->cfg.nq || !out) return fail(c, CHI0_EINVAL, "bad iq or NULL out");
@@ -1212,12 +1327,14 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_w, &c->d_part, &c->d_chi, &c->d_A, &c->d_colp, &c->d_rowp, &c->d_pinv,
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
                     &c->d_termq, &c->d_termw, &c->d_termc, &c->d_bgd, &c->d_bgperm, &c->d_bgkq,
-                    &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx};
+                    &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx, &c->d_sigR, &c->d_sigWd,
+                    &c->d_sigY, &c->d_sigI};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)
       if (e) cudaEventDestroy(e);
   chi0::tc_release(c);
+  chi0::sig_tc_release(c);
   cudaStream_t pst[] = {c->s_ct, c->s_dy};
   for (cudaStream_t t : pst)
     if (t) {

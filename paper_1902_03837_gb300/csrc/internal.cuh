@@ -150,4 +150,15 @@ cudaError_t launch_dyson_general(const double2* chi, const double* vsqrt, int ng
 // the tensor-core contraction, so that both can share an SM.
 cudaError_t dyson_prepare();
 
+// Self-energy kernel I (Eq. I_c; sigma.cu).  W^d of one frequency in FP64
+// from eps~^-1 (E) and V; Y(i, t) = sum_j W^d_ij conj(rho_t(j)) in plain
+// FP64 (rho in the rho kernel's order of the quasiparticle window, Y in
+// 64 x 64 tiles); I[g][a][b] = pref sum_i rho_(g,a)(i) Y(i, (g,b)).
+cudaError_t launch_sig_wd64(const double2* E, const double* vsqrt, int ng, double2* Wd, cudaStream_t s);
+cudaError_t launch_sig_gemm64(const double2* Wd, const double2* R, int ng, int64_t T, int nqp, int nb,
+                              double2* Y, cudaStream_t s);
+template <typename TR>
+cudaError_t launch_sig_dot(const TR* R, const double2* Y, int ng, int64_t T, int nqp, int nb, double pref,
+                           double2* out, cudaStream_t s);
+
 }  // namespace chi0

@@ -193,7 +193,10 @@ __device__ __forceinline__ void nsum(float& s, float& c, float x) {
 }
 
 // Work unit = one lower-triangle tile (I, J) x one range of k-blocks (a
-// split); unit u is tile u % ntiles of split u / ntiles, so the CTAs resident
+// split) -- or, with nI > 0, one tile of the full grid of nI row tiles of A
+// by ntiles / nI row tiles of B (I = tile % nI, J = tile / nI; A and B then
+// have their own row paddings mpad and mpad_b); unit u is tile u % ntiles of
+// split u / ntiles, so the CTAs resident
 // at one time read the same k-blocks (shared in L2).  The kernel is
 // persistent: CTA c takes units c, c + gridDim.x, ...; the stage ring and the
 // accumulator ping-pong run on across units, so the next unit's operands
@@ -211,7 +214,7 @@ __global__ void __maxnreg__(224)
 k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
               int total_kb, int kb_per_split, int mpad, double2* __restrict__ part, int ntiles,
-              int nunits, int* __restrict__ err) {
+              int nunits, int* __restrict__ err, int nI, int mpad_b) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -263,7 +266,13 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
       bool ok = true;
       for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         int I, J, kb0, nkb;
-        tri_decode(u % ntiles, I, J);
+        const int tile = u % ntiles;
+        if (nI > 0) {
+          I = tile % nI;
+          J = tile / nI;
+        } else {
+          tri_decode(tile, I, J);
+        }
         unit_range(u, kb0, nkb);
         for (int k = 0; k < nkb; ++k, ++gk) {
           const int s = gk % kStages;
@@ -274,11 +283,12 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
           }
           const uint32_t st = base + s * kStageBytes;
           mbar_expect_tx(bar_full + 8 * s, kStageBytes);
-          const int row = (kb0 + k) * mpad;  // k-blocked layout: block kb starts at row kb * mpad
+          // k-blocked layout: block kb starts at row kb * mpad (A) and kb * mpad_b (B)
+          const int row = (kb0 + k) * mpad, row_b = (kb0 + k) * mpad_b;
           tma_load_2d(st, &tm_ah, 0, row + I * kBM, bar_full + 8 * s);
           tma_load_2d(st + kTileBytes, &tm_al, 0, row + I * kBM, bar_full + 8 * s);
-          tma_load_2d(st + 2 * kTileBytes, &tm_bh, 0, row + J * kBN, bar_full + 8 * s);
-          tma_load_2d(st + 3 * kTileBytes, &tm_bl, 0, row + J * kBN, bar_full + 8 * s);
+          tma_load_2d(st + 2 * kTileBytes, &tm_bh, 0, row_b + J * kBN, bar_full + 8 * s);
+          tma_load_2d(st + 3 * kTileBytes, &tm_bl, 0, row_b + J * kBN, bar_full + 8 * s);
         }
       }
     }
@@ -626,7 +636,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       stage_begin(c, CHI0_STAGE_CONTRACT);
       k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
           t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
-          nunits, (int*)c->d_err.p);
+          nunits, (int*)c->d_err.p, 0, t.mpad);
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
       stage_begin(c, CHI0_STAGE_REDUCE);
       k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
@@ -661,6 +671,150 @@ void tc_release(chi0_ctx* c) {
   }
   delete t;
   c->tc = nullptr;
+}
+
+// ---- self-energy kernel I (Eq. I_c) -----------------------------------------
+// Y(i, t) = sum_j W^d_ij conj(rho_t(j)) is the same complex product as the
+// chi0 contraction, C_ij = sum_K A_K(i) conj(B_K(j)), with K = G' (ng values)
+// instead of the transitions: A = W^d (rows 2 i + c), B = rho of the
+// transitions t of the quasiparticle window (rows 2 t + c), the full grid of
+// 128 x 128 tiles, one k range per tile (no chunk partials: each tile's sum
+// is Y itself, in FP64).  Transitions are ordered t = ((k nb) + m) nqp + a,
+// so that the partners a of one (k, m) are adjacent columns of Y.
+
+namespace {
+
+struct SigTc {
+  DevBuf ah, al, bh, bl;
+  CUtensorMap m_ah, m_al, m_bh, m_bl;
+  int64_t kpad = 0, T = 0, mpad_b = 0;
+  int ng = 0, mpad_a = 0, nI = 0, nJ = 0, nsm = 1;
+};
+
+__device__ __forceinline__ void split_store(float x0, float x1, __nv_bfloat16* hi, __nv_bfloat16* lo, size_t off) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+  *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+  *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+}
+
+// B: row 2 t + c, column j holds rho_t(j).c (zero outside t < T, j < ng); the
+// rho kernel's row of transition t = ((k nb) + m) nqp + a is ((k nqp) + a) nb + m.
+__global__ void __launch_bounds__(256)
+k_sig_bsplit(const float2* __restrict__ R, int64_t T, int nqp, int nb, int ng, int64_t mpad_b,
+             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t r0 = (int64_t)blockIdx.x * 64;  // 64 rows = 32 transitions
+  const int kb = blockIdx.y;                    // 64 values of j
+  for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+    const int ml = e >> 5, jp = e & 31;
+    const int64_t m = r0 + ml, t = m >> 1;
+    const int j = kb * 64 + 2 * jp;
+    float x0 = 0.f, x1 = 0.f;
+    if (t < T) {
+      const int64_t a = t % nqp, g = t / nqp;
+      const float2* row = R + (((g / nb) * nqp + a) * nb + g % nb) * (int64_t)ng;
+      if (j < ng) x0 = (m & 1) ? row[j].y : row[j].x;
+      if (j + 1 < ng) x1 = (m & 1) ? row[j + 1].y : row[j + 1].x;
+    }
+    split_store(x0, x1, hi, lo, ((size_t)kb * mpad_b + m) * 64 + 2 * jp);
+  }
+}
+
+// A: row 2 i + c, column j holds W^d_ij.c, Eq. (W_delta) with W = V E V:
+// W^d_ij = V_i V_j [ (Im E_ij + Im E_ji) / 2 - i (Re E_ij - Re E_ji) / 2 ].
+__global__ void __launch_bounds__(256)
+k_sig_asplit(const double2* __restrict__ E, const double* __restrict__ v, int ng, int mpad_a,
+             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int r0 = blockIdx.x * 64;
+  const int kb = blockIdx.y;
+  for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+    const int ml = e >> 5, jp = e & 31;
+    const int m = r0 + ml, i = m >> 1;
+    const int j = kb * 64 + 2 * jp;
+    float x[2] = {0.f, 0.f};
+    if (i < ng) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int jj = j + q;
+        if (jj < ng) {
+          const double2 a = E[(size_t)i * ng + jj], b = E[(size_t)jj * ng + i];
+          const double f = 0.5 * v[i] * v[jj];
+          x[q] = (float)((m & 1) ? -f * (a.x - b.x) : f * (a.y + b.y));
+        }
+      }
+    }
+    split_store(x[0], x[1], hi, lo, ((size_t)kb * mpad_a + m) * 64 + 2 * jp);
+  }
+}
+
+}  // namespace
+
+chi0_status sig_tc_plan(chi0_ctx* c, int64_t T, int ng) {
+  if (!c->sig_tc) c->sig_tc = new SigTc();
+  SigTc& t = *static_cast<SigTc*>(c->sig_tc);
+  t.T = T;
+  t.ng = ng;
+  t.kpad = (ng + kBK - 1) / kBK * kBK;
+  t.nI = (ng + 63) / 64;
+  t.nJ = (int)std::min<int64_t>((T + 63) / 64, 0x7fffffff);
+  t.mpad_a = t.nI * kBM;
+  t.mpad_b = (int64_t)t.nJ * kBN;
+  // TMA row coordinates and tile indices are 32-bit
+  if ((T + 63) / 64 > 0x7fffffff / t.nI || (t.kpad / kBK) * t.mpad_b > 0x7fffffff)
+    return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions in the quasiparticle window for one contraction");
+  chi0_status s;
+  const size_t opa = (size_t)t.mpad_a * t.kpad * 2, opb = (size_t)t.mpad_b * t.kpad * 2;
+  if ((s = ctx_ensure(c, t.ah, opa, "W^delta hi")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.al, opa, "W^delta lo")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.bh, opb, "rho hi")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.bl, opb, "rho lo")) != CHI0_OK) return s;
+  if (!make_map(&t.m_ah, t.ah.p, t.kpad, t.mpad_a) || !make_map(&t.m_al, t.al.p, t.kpad, t.mpad_a) ||
+      !make_map(&t.m_bh, t.bh.p, t.kpad, (int)t.mpad_b) || !make_map(&t.m_bl, t.bl.p, t.kpad, (int)t.mpad_b))
+    return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
+  int dev = 0, nsm = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  t.nsm = std::max(1, nsm);
+  cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
+  return CHI0_OK;
+}
+
+cudaError_t sig_tc_split_b(chi0_ctx* c, const float2* R, int nqp, int nb) {
+  SigTc& t = *static_cast<SigTc*>(c->sig_tc);
+  k_sig_bsplit<<<dim3((unsigned)(t.mpad_b / 64), (unsigned)(t.kpad / 64)), 256, 0, c->st>>>(
+      R, t.T, nqp, nb, t.ng, t.mpad_b, (__nv_bfloat16*)t.bh.p, (__nv_bfloat16*)t.bl.p);
+  return cudaGetLastError();
+}
+
+cudaError_t sig_tc_split_a(chi0_ctx* c, const double2* E, const double* vsqrt) {
+  SigTc& t = *static_cast<SigTc*>(c->sig_tc);
+  k_sig_asplit<<<dim3((unsigned)(t.mpad_a / 64), (unsigned)(t.kpad / 64)), 256, 0, c->st>>>(
+      E, vsqrt, t.ng, t.mpad_a, (__nv_bfloat16*)t.ah.p, (__nv_bfloat16*)t.al.p);
+  return cudaGetLastError();
+}
+
+cudaError_t sig_tc_contract(chi0_ctx* c, double2* Y) {
+  SigTc& t = *static_cast<SigTc*>(c->sig_tc);
+  const int ntiles = t.nI * t.nJ;
+  const int total_kb = (int)(t.kpad / kBK);
+  const unsigned grid = (unsigned)std::min(ntiles, t.nsm);
+  k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah, t.m_al, t.m_bh, t.m_bl, total_kb, total_kb,
+                                                        t.mpad_a, Y, ntiles, ntiles, (int*)c->d_err.p, t.nI,
+                                                        (int)t.mpad_b);
+  return cudaGetLastError();
+}
+
+void sig_tc_release(chi0_ctx* c) {
+  if (!c->sig_tc) return;
+  SigTc* t = static_cast<SigTc*>(c->sig_tc);
+  DevBuf* bufs[] = {&t->ah, &t->al, &t->bh, &t->bl};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  delete t;
+  c->sig_tc = nullptr;
 }
 
 }  // namespace chi0
