@@ -347,6 +347,37 @@ def run_ours(args, rank, world, dist):
             t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
+    sigma_line = None
+    if args.sigma:
+        # the self-energy kernel I (Eq. I_c) on the real-axis eps~^-1 of this
+        # step: the plasmon-pole model's matrices, or the direct real-axis ones
+        lo, hi = args.sigma
+        src = model_d if args.ppa else inv_d
+        nws, nqp = int(src.shape[0]), hi - lo
+        out_s = torch.empty((nws, s.nk, s.nb, nqp, nqp), dtype=torch.complex128, device=dev)
+        ctx.build_sigma_i(0, lo, hi, src, out_s)   # plans the buffers
+        ctx.synchronize()
+        ctx.get_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.sigma_steps):
+            ctx.build_sigma_i(0, lo, hi, src, out_s)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sig_ms = e0.elapsed_time(e1) / args.sigma_steps
+        sms, _, _, _ = ctx.get_stats()
+        sms = {k: v / args.sigma_steps for k, v in sms.items()}
+        T = s.nk * s.nb * nqp
+        n_i, n_j = -(-ng // 64), -(-T // 64)
+        alg = 8.0 * ng * ng * T * nws                     # complex N_G^2 T multiply-adds per frequency
+        issued = 3 * 2 * 128 * 128 * (-(-ng // 64) * 64) * n_i * n_j * nws
+        ybytes = n_i * n_j * 4096 * (8.0 if args.precision == "mixed" else 16.0) * nws   # Y tiles read by the dot
+        sigma_line = {"window": [lo, hi], "n_freqs": nws, "n_transitions": T, "ms_per_call": sig_ms,
+                      "stage_ms_per_call": {"rho": sms["rho"], "split": sms["weights"],
+                                            "contract": sms["contract"], "dot": sms["reduce"]},
+                      "contract_tflops": alg / (sms["contract"] * 1e-3) / 1e12,
+                      "contract_issued_tflops": issued / (sms["contract"] * 1e-3) / 1e12,
+                      "dot_y_gbs": ybytes / (sms["reduce"] * 1e-3) / 1e9}
     ctx.get_stats()
     ctx.close()
 
@@ -423,6 +454,12 @@ def run_ours(args, rank, world, dist):
     }
     if ppa_line is not None:
         line["ppa"] = ppa_line
+    if sigma_line is not None:
+        sg = sigma_line
+        sg["contract_issued_frac"] = sg["contract_issued_tflops"] / pk["bf16_tflops_sustained"]
+        sg["contract_peak_source"] = f"BF16 dense sustained ({pk['source']})"
+        sg["dot_y_hbm_frac"] = sg["dot_y_gbs"] / pk["hbm_gbs"]
+        line["sigma"] = sg
     if not args.no_cpu_baseline:
         import oracle as O
         G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
@@ -457,9 +494,15 @@ def main():
     ap.add_argument("--ppa", type=int, default=0, metavar="NW",
                     help="plasmon-pole path: chi0 and eps^-1 at w = 0 and i 1 Ha only, the Godby-Needs fit and "
                          "the model on NW real frequencies on (0, 100] eV")
+    ap.add_argument("--sigma", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    metavar="LO,HI", help="then time the self-energy kernel I (Eq. I_c) for the bands [LO, HI) at k "
+                                          "on the real-axis eps~^-1 of --ppa or --real-axis")
+    ap.add_argument("--sigma-steps", type=int, default=2)
     args = ap.parse_args()
     if args.ppa and (args.real_axis or args.ppa < 0):
         ap.error("--ppa takes a positive count and excludes --real-axis")
+    if args.sigma and not (args.ppa or args.real_axis):
+        ap.error("--sigma needs real-axis frequencies: --ppa NW or --real-axis")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

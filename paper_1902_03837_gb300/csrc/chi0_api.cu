@@ -1121,7 +1121,8 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
   const int64_t nI = (ng + 63) / 64, nJ = (T + 63) / 64;
   const size_t osz = (size_t)c->nk * nb * nqp * nqp * 16;   // I of one frequency
   if ((s = ensure(c, c->d_sigR, (size_t)T * ng * cb, "quasiparticle rho")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_sigY, (size_t)nI * nJ * 4096 * 16, "W^delta rho* tiles")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_sigY, (size_t)nI * nJ * 4096 * cb * 2, "W^delta rho* tiles")) != CHI0_OK) return s;
+  if ((s = ensure(c, c->d_sigRT, (size_t)nI * nJ * 4096 * cb, "rho tiles")) != CHI0_OK) return s;
   if (!out_on_device && (s = ensure(c, c->d_sigI, osz, "I staging")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_vsqrt, (size_t)ng * 8, "coulomb")) != CHI0_OK) return s;
   if (c->fp64) {
@@ -1164,7 +1165,12 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
                                               (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p,
                                               (const float2*)c->d_tw2.p, (float2*)c->d_sigR.p, c->st);
   if (e != cudaSuccess) return cuda_fail(c, e, "quasiparticle rho launch");
-  chi0::stage_end(c, CHI0_STAGE_RHO, 1);
+  e = c->fp64 ? chi0::launch_sig_rhot<double2>((const double2*)c->d_sigR.p, T, nqp, nb, ng, (double2*)c->d_sigRT.p,
+                                               c->st)
+              : chi0::launch_sig_rhot<float2>((const float2*)c->d_sigR.p, T, nqp, nb, ng, (float2*)c->d_sigRT.p,
+                                              c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rho tile copy launch");
+  chi0::stage_end(c, CHI0_STAGE_RHO, 2);
   if (!c->fp64) {
     chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
     if ((e = chi0::sig_tc_split_b(c, (const float2*)c->d_sigR.p, nqp, nb)) != cudaSuccess)
@@ -1174,7 +1180,7 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
   const double pref = -1.0 / ((double)c->nk * c->omega_cell);   // Eq. (I_c)
   const size_t n2 = (size_t)ng * ng;
   const double* v = (const double*)c->d_vsqrt.p;
-  double2* Y = (double2*)c->d_sigY.p;
+  void* Y = c->d_sigY.p;   // FP64 (FP64 form) or FP32 (mixed form) tiles
   for (int iw = 0; iw < nw; ++iw) {
     const double2* E = (const double2*)eps_inv + iw * n2;
     double2* I = out_on_device ? (double2*)((char*)out + iw * osz) : (double2*)c->d_sigI.p;
@@ -1184,13 +1190,15 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
     chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
     e = c->fp64 ? chi0::launch_sig_gemm64((const double2*)c->d_sigWd.p, (const double2*)c->d_sigR.p, ng, T, nqp, nb,
-                                          Y, c->st)
-                : chi0::sig_tc_contract(c, Y);
+                                          (double2*)Y, c->st)
+                : chi0::sig_tc_contract(c, (float2*)Y);
     if (e != cudaSuccess) return cuda_fail(c, e, "W^delta rho* contraction launch");
     chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
     chi0::stage_begin(c, CHI0_STAGE_REDUCE);
-    e = c->fp64 ? chi0::launch_sig_dot<double2>((const double2*)c->d_sigR.p, Y, ng, T, nqp, nb, pref, I, c->st)
-                : chi0::launch_sig_dot<float2>((const float2*)c->d_sigR.p, Y, ng, T, nqp, nb, pref, I, c->st);
+    e = c->fp64 ? chi0::launch_sig_dot<double2, double2>((const double2*)c->d_sigRT.p, (const double2*)Y, ng, T, nqp,
+                                                         pref, I, c->st)
+                : chi0::launch_sig_dot<float2, float2>((const float2*)c->d_sigRT.p, (const float2*)Y, ng, T, nqp, pref,
+                                                       I, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "I launch");
     chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
     if (!out_on_device)
@@ -1200,9 +1208,9 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
   // contraction of N_G^2 T multiply-adds and one of N_G T nqp per frequency
   c->stage[CHI0_STAGE_RHO].bytes = (double)T * ng * cb;
   c->stage[CHI0_STAGE_CONTRACT].flops = 8.0 * (double)ng * ng * (double)T * nw;
-  c->stage[CHI0_STAGE_CONTRACT].bytes = ((double)ng * ng * 16 + (double)T * ng * cb + (double)T * ng * 16) * nw;
+  c->stage[CHI0_STAGE_CONTRACT].bytes = ((double)ng * ng * 16 + (double)T * ng * cb + (double)T * ng * 2 * cb) * nw;
   c->stage[CHI0_STAGE_REDUCE].flops = 8.0 * (double)ng * (double)T * nqp * nw;
-  c->stage[CHI0_STAGE_REDUCE].bytes = ((double)T * ng * 16 + (double)osz) * nw;
+  c->stage[CHI0_STAGE_REDUCE].bytes = ((double)T * ng * 2 * cb + (double)osz) * nw;
   if (!out_on_device) {
     CK(cudaStreamSynchronize(c->st), "synchronize");
     return check_device_error(c);
@@ -1328,7 +1336,7 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
                     &c->d_termq, &c->d_termw, &c->d_termc, &c->d_bgd, &c->d_bgperm, &c->d_bgkq,
                     &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx, &c->d_sigR, &c->d_sigWd,
-                    &c->d_sigY, &c->d_sigI};
+                    &c->d_sigY, &c->d_sigI, &c->d_sigRT};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)

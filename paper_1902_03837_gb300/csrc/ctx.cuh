@@ -73,7 +73,7 @@ struct chi0_ctx {
   // rho of the quasiparticle window n in [qp_lo, qp_lo + nqp) at k and every
   // band m at k - q, W^delta and Y = W^delta conj(rho) per frequency
   RhoGeom sig_geom{};
-  DevBuf d_sigR, d_sigWd, d_sigY, d_sigI;
+  DevBuf d_sigR, d_sigRT, d_sigWd, d_sigY, d_sigI;
   void* sig_tc = nullptr;
 
   // per-stage device time: CUDA event pairs on the context's stream, summed
@@ -118,13 +118,13 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
 void tc_release(chi0_ctx* c);
 // self-energy kernel I (Eq. I_c) on the tensor cores: Y(i, t) = sum_j
 // W^d_ij conj(rho_t(j)) for T transitions of the quasiparticle window, written
-// as 64 x 64 complex tiles, tile (i / 64) + (t / 64) * ceil(ng / 64)
+// in FP32 as 64 x 64 complex tiles, tile (i / 64) + (t / 64) * ceil(ng / 64)
 chi0_status sig_tc_plan(chi0_ctx* c, int64_t T, int ng);
 // rho of the window (the rho kernel's order ((k nqp) + a) nb + m) into the B operand
 cudaError_t sig_tc_split_b(chi0_ctx* c, const float2* R, int nqp, int nb);
 // W^d of one frequency from eps~^-1 (E) and V into the A operand
 cudaError_t sig_tc_split_a(chi0_ctx* c, const double2* E, const double* vsqrt);
-cudaError_t sig_tc_contract(chi0_ctx* c, double2* Y);
+cudaError_t sig_tc_contract(chi0_ctx* c, float2* Y);
 void sig_tc_release(chi0_ctx* c);
 // learned terminator: network kernels and the correction of a built chi0
 int mlp_nparams();

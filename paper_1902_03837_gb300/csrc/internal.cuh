@@ -157,8 +157,11 @@ cudaError_t dyson_prepare();
 cudaError_t launch_sig_wd64(const double2* E, const double* vsqrt, int ng, double2* Wd, cudaStream_t s);
 cudaError_t launch_sig_gemm64(const double2* Wd, const double2* R, int ng, int64_t T, int nqp, int nb,
                               double2* Y, cudaStream_t s);
+// rho of the window (rho kernel order) into the tile layout of Y (RT)
 template <typename TR>
-cudaError_t launch_sig_dot(const TR* R, const double2* Y, int ng, int64_t T, int nqp, int nb, double pref,
-                           double2* out, cudaStream_t s);
+cudaError_t launch_sig_rhot(const TR* R, int64_t T, int nqp, int nb, int ng, TR* RT, cudaStream_t s);
+template <typename TR, typename TY>
+cudaError_t launch_sig_dot(const TR* RT, const TY* Y, int ng, int64_t T, int nqp, double pref, double2* out,
+                           cudaStream_t s);
 
 }  // namespace chi0

@@ -13,7 +13,9 @@
 // Transitions of the window are ordered t = ((k nb) + m) nqp + a (partners of
 // one (k, m) adjacent); the rho kernel writes them in the order
 // ((k nqp) + a) nb + m.  Y is stored as 64 x 64 complex tiles, tile
-// (i / 64) + (t / 64) * nI, nI = ceil(ng / 64), entry (i % 64) * 64 + t % 64.
+// (i / 64) + (t / 64) * nI, nI = ceil(ng / 64), entry (i % 64) * 64 + t % 64,
+// in FP32 (mixed form) or FP64; rho is copied once per call into the same
+// layout (RT) for the dot products.
 #include "internal.cuh"
 
 namespace chi0 {
@@ -67,95 +69,118 @@ k_sig_gemm64(const double2* __restrict__ Wd, const double2* __restrict__ R, int 
     Y[((size_t)(t / 64) * nI + i / 64) * 4096 + (size_t)(i % 64) * 64 + t % 64] = make_double2(sx, sy);
 }
 
-constexpr int kDotChunk = 32;   // values of i staged per pass
-constexpr int kDotA = 8;        // partners a per pass
+constexpr int kDotUnroll = 8;   // values of i per thread between FP64 sums
 
-// I[g][a][b] = pref sum_i rho_{(g,a)}(i) Y(i, (g,b)), g = (k, m): one block
-// per 64 columns t = (g, b); 256 threads = 64 columns x 4 phases over i.
-// The rho rows of the groups these columns touch are staged in shared memory
-// per 32 values of i.  Products in the element type of rho (FP32 in the mixed
-// form: at most 8 terms per thread and chunk), sums over chunks in FP64.
+__device__ __forceinline__ size_t tile_off(int64_t t, int i, int nI) {
+  return ((size_t)(t >> 6) * nI + (i >> 6)) * 4096 + (size_t)(i & 63) * 64 + (t & 63);
+}
+
+// rho of the window in the tile layout of Y: RT(i, t) = rho_t(i), t in the
+// group-major order (one pass per call; the dot then reads its columns
+// coalesced).  32 x 32 blocks through shared memory.
 template <typename TR>
 __global__ void __launch_bounds__(256)
-k_sig_dot(const TR* __restrict__ R, const double2* __restrict__ Y, int ng, int64_t T, int nqp, int nb, int nI,
-          double pref, double2* __restrict__ out) {
-  using F = decltype(TR::x);
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  TR* rs = reinterpret_cast<TR*>(sm_raw);   // [rows][kDotChunk]
-  const int64_t c0 = (int64_t)blockIdx.x * 64;
-  const int64_t c1 = c0 + 64 < T ? c0 + 64 : T;
-  const int64_t g_lo = c0 / nqp, g_hi = (c1 - 1) / nqp;
-  const int rows = (int)(g_hi - g_lo + 1) * nqp;
-  const int jl = threadIdx.x & 63, ph = threadIdx.x >> 6;
-  const int64_t tcol = c0 + jl;
-  const bool live = tcol < T;
-  const int64_t g = live ? tcol / nqp : g_lo;
-  const int b = live ? (int)(tcol % nqp) : 0;
-  const int lrow0 = (int)(g - g_lo) * nqp;
-  const double2* Ycol = Y + (size_t)(c0 / 64) * nI * 4096 + jl;
-  for (int a0 = 0; a0 < nqp; a0 += kDotA) {
-    double sx[kDotA], sy[kDotA];
-#pragma unroll
-    for (int q = 0; q < kDotA; ++q) sx[q] = sy[q] = 0.0;
-    for (int i0 = 0; i0 < ng; i0 += kDotChunk) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < rows * kDotChunk; e += 256) {
-        const int r = e / kDotChunk, il = e % kDotChunk;
-        const int i = i0 + il;
-        TR v;
-        v.x = 0;
-        v.y = 0;
-        if (i < ng) v = R[rho_row((g_lo + r / nqp) * nqp + r % nqp, nqp, nb) * ng + i];
-        rs[e] = v;
-      }
-      __syncthreads();
-      if (live) {
-        F cx[kDotA], cy[kDotA];
-#pragma unroll
-        for (int q = 0; q < kDotA; ++q) cx[q] = cy[q] = 0;
-        for (int il = ph; il < kDotChunk && i0 + il < ng; il += 4) {
-          const int i = i0 + il;
-          const double2 yd = Ycol[(size_t)(i >> 6) * 4096 + (size_t)(i & 63) * 64];
-          const F yx = (F)yd.x, yy = (F)yd.y;
-#pragma unroll
-          for (int q = 0; q < kDotA; ++q)
-            if (a0 + q < nqp) {
-              const TR r = rs[(lrow0 + a0 + q) * kDotChunk + il];
-              cx[q] += r.x * yx - r.y * yy;
-              cy[q] += r.x * yy + r.y * yx;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kDotA; ++q) {
-          sx[q] += (double)cx[q];
-          sy[q] += (double)cy[q];
-        }
-      }
-    }
-    // sum the four phases
-    __syncthreads();
-    double2* red = reinterpret_cast<double2*>(sm_raw);   // [4][64][kDotA]
-#pragma unroll
-    for (int q = 0; q < kDotA; ++q) red[(ph * 64 + jl) * kDotA + q] = make_double2(sx[q], sy[q]);
-    __syncthreads();
-    if (ph == 0 && live)
-      for (int q = 0; q < kDotA && a0 + q < nqp; ++q) {
-        double x = 0.0, y = 0.0;
-        for (int p = 0; p < 4; ++p) {
-          const double2 v = red[(p * 64 + jl) * kDotA + q];
-          x += v.x;
-          y += v.y;
-        }
-        out[((size_t)g * nqp + a0 + q) * nqp + b] = make_double2(pref * x, pref * y);
-      }
+k_sig_rhot(const TR* __restrict__ R, int64_t T, int nqp, int nb, int ng, int nI, TR* __restrict__ RT) {
+  __shared__ TR tl[32][33];
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  const int i0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows per pass
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t t = t0 + r;
+    const int i = i0 + tx;
+    TR v;
+    v.x = 0;
+    v.y = 0;
+    if (t < T && i < ng) v = R[rho_row(t, nqp, nb) * ng + i];
+    tl[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r;
+    const int64_t t = t0 + tx;
+    if (t < T && i < ng) RT[tile_off(t, i, nI)] = tl[tx][r];
   }
 }
 
-template <typename TR>
-size_t dot_smem(int nqp) {
-  const size_t rows = (size_t)(63 / nqp + 2) * nqp;
-  const size_t a = rows * kDotChunk * sizeof(TR), r = (size_t)4 * 64 * kDotA * 16;
-  return a > r ? a : r;
+// Running sum of the dot products: FP64 in the FP64 form; in the mixed form
+// FP32 with Neumaier compensation (GB300's FP64 units are too few to convert
+// and add every partial sum in FP64 at the rate the loads arrive).
+template <typename F>
+struct DotSum {
+  F s = 0, c = 0;
+  __device__ __forceinline__ void add(F x) {
+    if constexpr (sizeof(F) == 4) {
+      const F t = s + x;
+      c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// I[g][a][b] = pref sum_i rho_{(g,a)}(i) Y(i, (g,b)), g = (k, m): one block
+// per 64 columns t = (g, b); 256 threads = 64 columns x 4 phases over i.
+// Each thread reads its column of Y and the columns (g, a) of RT (tile
+// layout, both coalesced across the warp), A partners per pass.  Products in
+// the element type of rho, summed kDotUnroll at a time into a DotSum.
+template <typename TR, typename TY, int A>
+__global__ void __launch_bounds__(256)
+k_sig_dot(const TR* __restrict__ RT, const TY* __restrict__ Y, int ng, int64_t T, int nqp, int nI, double pref,
+          double2* __restrict__ out) {
+  using F = decltype(TR::x);
+  __shared__ double2 red[4][64][A];
+  const int jl = threadIdx.x & 63, ph = threadIdx.x >> 6;
+  const int64_t t = (int64_t)blockIdx.x * 64 + jl;
+  const bool live = t < T;
+  const int64_t g = live ? t / nqp : 0;
+  const int b = live ? (int)(t % nqp) : 0;
+  const TY* Ycol = Y + tile_off(t, 0, nI);
+  for (int a0 = 0; a0 < nqp; a0 += A) {
+    const TR* col[A];   // the partners (g, a0 + q) in RT
+#pragma unroll
+    for (int q = 0; q < A; ++q) col[q] = RT + tile_off(g * nqp + ((a0 + q < nqp) ? a0 + q : 0), 0, nI);
+    DotSum<F> sx[A], sy[A];
+    if (live) {
+      for (int i0 = ph; i0 < ng; i0 += 4 * kDotUnroll) {
+        F cx[A], cy[A];
+#pragma unroll
+        for (int q = 0; q < A; ++q) cx[q] = cy[q] = 0;
+#pragma unroll
+        for (int r = 0; r < kDotUnroll; ++r) {
+          const int i = i0 + 4 * r;
+          if (i < ng) {
+            const size_t ro = (size_t)(i >> 6) * 4096 + (size_t)(i & 63) * 64;
+            const TY yd = Ycol[ro];
+            const F yx = (F)yd.x, yy = (F)yd.y;
+#pragma unroll
+            for (int q = 0; q < A; ++q)
+              if (a0 + q < nqp) {
+                const TR v = col[q][ro];
+                cx[q] += v.x * yx - v.y * yy;
+                cy[q] += v.x * yy + v.y * yx;
+              }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+          sx[q].add(cx[q]);
+          sy[q].add(cy[q]);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < A; ++q) red[ph][jl][q] = make_double2(sx[q].value(), sy[q].value());
+    __syncthreads();
+    if (ph == 0 && live)
+      for (int q = 0; q < A && a0 + q < nqp; ++q) {
+        const double x = red[0][jl][q].x + red[1][jl][q].x + red[2][jl][q].x + red[3][jl][q].x;
+        const double y = red[0][jl][q].y + red[1][jl][q].y + red[2][jl][q].y + red[3][jl][q].y;
+        out[((size_t)g * nqp + a0 + q) * nqp + b] = make_double2(pref * x, pref * y);
+      }
+  }
 }
 
 }  // namespace
@@ -175,19 +200,30 @@ cudaError_t launch_sig_gemm64(const double2* Wd, const double2* R, int ng, int64
 }
 
 template <typename TR>
-cudaError_t launch_sig_dot(const TR* R, const double2* Y, int ng, int64_t T, int nqp, int nb, double pref,
-                           double2* out, cudaStream_t s) {
+cudaError_t launch_sig_rhot(const TR* R, int64_t T, int nqp, int nb, int ng, TR* RT, cudaStream_t s) {
   const int nI = (ng + 63) / 64;
-  const size_t smem = dot_smem<TR>(nqp);
-  cudaError_t e = cudaFuncSetAttribute(k_sig_dot<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_sig_dot<TR><<<(unsigned)((T + 63) / 64), 256, smem, s>>>(R, Y, ng, T, nqp, nb, nI, pref, out);
+  k_sig_rhot<TR><<<dim3((unsigned)((T + 31) / 32), (unsigned)((ng + 31) / 32)), 256, 0, s>>>(R, T, nqp, nb, ng, nI,
+                                                                                              RT);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_sig_dot<float2>(const float2*, const double2*, int, int64_t, int, int, double, double2*,
-                                            cudaStream_t);
-template cudaError_t launch_sig_dot<double2>(const double2*, const double2*, int, int64_t, int, int, double,
-                                             double2*, cudaStream_t);
+template <typename TR, typename TY>
+cudaError_t launch_sig_dot(const TR* RT, const TY* Y, int ng, int64_t T, int nqp, double pref, double2* out,
+                           cudaStream_t s) {
+  const int nI = (ng + 63) / 64;
+  const unsigned grid = (unsigned)((T + 63) / 64);
+  if (nqp <= 4)   // fewer partners per pass: fewer registers, more resident blocks
+    k_sig_dot<TR, TY, 4><<<grid, 256, 0, s>>>(RT, Y, ng, T, nqp, nI, pref, out);
+  else
+    k_sig_dot<TR, TY, 8><<<grid, 256, 0, s>>>(RT, Y, ng, T, nqp, nI, pref, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sig_rhot<float2>(const float2*, int64_t, int, int, int, float2*, cudaStream_t);
+template cudaError_t launch_sig_rhot<double2>(const double2*, int64_t, int, int, int, double2*, cudaStream_t);
+template cudaError_t launch_sig_dot<float2, float2>(const float2*, const float2*, int, int64_t, int, double,
+                                                    double2*, cudaStream_t);
+template cudaError_t launch_sig_dot<double2, double2>(const double2*, const double2*, int, int64_t, int, double,
+                                                      double2*, cudaStream_t);
 
 }  // namespace chi0

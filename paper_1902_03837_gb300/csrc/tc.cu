@@ -214,7 +214,7 @@ __global__ void __maxnreg__(224)
 k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
               int total_kb, int kb_per_split, int mpad, double2* __restrict__ part, int ntiles,
-              int nunits, int* __restrict__ err, int nI, int mpad_b) {
+              int nunits, int* __restrict__ err, int nI, int mpad_b, int f32out) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -387,16 +387,28 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
       }
       if (!ok) break;
       const int il = (q * 32 + lane) >> 1;  // complex row of the tile
-      double2* out = part + ((size_t)(u / ntiles) * ntiles + (u % ntiles)) * (size_t)(kBM / 2) * (kBN / 2) +
-                     (size_t)il * (kBN / 2) + (odd ? 4 : 0);
+      const size_t obase = ((size_t)(u / ntiles) * ntiles + (u % ntiles)) * (size_t)(kBM / 2) * (kBN / 2) +
+                           (size_t)il * (kBN / 2) + (odd ? 4 : 0);
+      if (f32out) {  // the compensated sums rounded to FP32 (the tile layout of part, 8-byte entries)
+        float2* out = reinterpret_cast<float2*>(part) + obase;
 #pragma unroll
-      for (int cb = 0; cb < kBN / 16; ++cb)
+        for (int cb = 0; cb < kBN / 16; ++cb)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int e = cb * 4 + jj;
-          out[cb * 8 + jj] = make_double2((double)accs[e][0] + (double)accc[e][0],
-                                          (double)accs[e][1] + (double)accc[e][1]);
-        }
+          for (int jj = 0; jj < 4; ++jj) {
+            const int e = cb * 4 + jj;
+            out[cb * 8 + jj] = make_float2(accs[e][0] + accc[e][0], accs[e][1] + accc[e][1]);
+          }
+      } else {
+        double2* out = part + obase;
+#pragma unroll
+        for (int cb = 0; cb < kBN / 16; ++cb)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int e = cb * 4 + jj;
+            out[cb * 8 + jj] = make_double2((double)accs[e][0] + (double)accc[e][0],
+                                            (double)accs[e][1] + (double)accc[e][1]);
+          }
+      }
     }
   }
   tc_fence_before();
@@ -636,7 +648,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       stage_begin(c, CHI0_STAGE_CONTRACT);
       k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
           t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
-          nunits, (int*)c->d_err.p, 0, t.mpad);
+          nunits, (int*)c->d_err.p, 0, t.mpad, 0);
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
       stage_begin(c, CHI0_STAGE_REDUCE);
       k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
@@ -679,7 +691,7 @@ void tc_release(chi0_ctx* c) {
 // instead of the transitions: A = W^d (rows 2 i + c), B = rho of the
 // transitions t of the quasiparticle window (rows 2 t + c), the full grid of
 // 128 x 128 tiles, one k range per tile (no chunk partials: each tile's sum
-// is Y itself, in FP64).  Transitions are ordered t = ((k nb) + m) nqp + a,
+// is Y itself, rounded to FP32).  Transitions are ordered t = ((k nb) + m) nqp + a,
 // so that the partners a of one (k, m) are adjacent columns of Y.
 
 namespace {
@@ -796,14 +808,14 @@ cudaError_t sig_tc_split_a(chi0_ctx* c, const double2* E, const double* vsqrt) {
   return cudaGetLastError();
 }
 
-cudaError_t sig_tc_contract(chi0_ctx* c, double2* Y) {
+cudaError_t sig_tc_contract(chi0_ctx* c, float2* Y) {
   SigTc& t = *static_cast<SigTc*>(c->sig_tc);
   const int ntiles = t.nI * t.nJ;
   const int total_kb = (int)(t.kpad / kBK);
   const unsigned grid = (unsigned)std::min(ntiles, t.nsm);
   k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah, t.m_al, t.m_bh, t.m_bl, total_kb, total_kb,
-                                                        t.mpad_a, Y, ntiles, ntiles, (int*)c->d_err.p, t.nI,
-                                                        (int)t.mpad_b);
+                                                        t.mpad_a, reinterpret_cast<double2*>(Y), ntiles, ntiles,
+                                                        (int*)c->d_err.p, t.nI, (int)t.mpad_b, 1);
   return cudaGetLastError();
 }
 
