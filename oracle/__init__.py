@@ -22,7 +22,9 @@ theory calculations using the yambo code", J. Phys.: Condens. Matter 31,
 * the Godby-Needs plasmon-pole fit of eps^-1 at w = 0 and w = i w_p (Full
   frequency GW subsection);
 * the screened interaction W, its delta-like part and the self-energy kernel
-  I of Eqs. (W_def), (W_delta), (I_c).
+  I of Eqs. (W_def), (W_delta), (I_c);
+* the degenerate-pole grouping of Appendix B and the double-grid frequency
+  factor.
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 against invariants, closed forms or independent routes.
@@ -40,3 +42,7 @@ from .dyson import eps_tilde, eps_inv_gauss_jordan, eps_inv_rpa_route  # noqa: F
 from .bg_terminator import diag_density, extrapolar_weights, delta_chi_bg, chi0_bg  # noqa: F401
 from .ppa import ppa_fit, ppa_eval  # noqa: F401
 from .self_energy import screened_w, w_delta, i_kernel  # noqa: F401
+from .poles import (  # noqa: F401
+    pole_energies, pole_groups, weights_grouped, weights_double_grid, chi0_weighted, chi0_grouped,
+    chi0_double_grid,
+)
