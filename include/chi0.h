@@ -337,6 +337,31 @@ chi0_status chi0_set_terminator(chi0_ctx* ctx, const float* params, int bf16);
  * Errors: CHI0_EINVAL (eps_bar not finite, learned terminator set). */
 chi0_status chi0_set_bg_terminator(chi0_ctx* ctx, int on, double eps_bar);
 
+/* ---- Degenerate-pole grouping and the double grid ------------------------------
+ * Appendix B (Eqs. X_IP_split, split1, split2): chi0 is a sum of frequency
+ * factors F(w) of the pole energies d_t = eps_{m,k-q} - eps_{n,k} times
+ * frequency-independent rho rho^* terms, and poles closer than eps_thresh
+ * share one factor.  With eps_thresh > 0 the poles of the transitions that
+ * carry weight are sorted by energy (ties in transition order); a group
+ * opens at the smallest pole not yet taken (its representative) and takes
+ * every following pole with d_t - d_rep < eps_thresh; every member uses the
+ * representative's factor.  eps_thresh = 0 (the default) switches it off.
+ * The paper's input CGrdSpXd = 100 means eps_thresh = 1e-5 Ha.
+ * The double grid (the dense-grid paragraph of the Bethe-Salpeter section)
+ * replaces the factor of each transition by its mean over nd transitions of
+ * a dense grid: eps_dense is a host array [nk][nd][nbands] (Ha) holding the
+ * energies of nd dense points around each coarse k (point j of k and point j
+ * of k - q form one dense transition); the occupation factor stays that of
+ * the coarse grid.  nd = 0 switches it off; the two options exclude each
+ * other.  Both act on the weights of every following chi0_build_chi0 /
+ * chi0_build_invert (and batch creation); the tensor-core contraction is
+ * unchanged (it sums over every transition either way).
+ * Errors: CHI0_EINVAL (threshold negative or not finite; nd out of
+ * [0, 4096]; NULL or non-finite energies; both options set), CHI0_ENOMEM,
+ * CHI0_ECUDA. */
+chi0_status chi0_set_pole_grouping(chi0_ctx* ctx, double eps_thresh);
+chi0_status chi0_set_double_grid(chi0_ctx* ctx, int nd, const double* eps_dense);
+
 /* ---- Self-energy kernel I (full-frequency GW) --------------------------------
  * Full frequency GW subsection, Eqs. (W_def), (W_delta), (I_c):
  *   I^{ab k}_{m q}(w) = -1/(N_k Omega) sum_{G,G'} W^d_GG'(q,w) rho_{amk}(q,G) conj(rho_{bmk}(q,G')),

@@ -30,7 +30,7 @@ EXPORTS = (
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator", "chi0_set_bg_terminator",
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
-    "chi0_ppa_fit", "chi0_ppa_eval", "chi0_build_sigma_i",
+    "chi0_ppa_fit", "chi0_ppa_eval", "chi0_build_sigma_i", "chi0_set_pole_grouping", "chi0_set_double_grid",
 )
 
 
@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_batch_destroy.argtypes = [P]
     lib.chi0_ppa_fit.argtypes = [P, P, I, D, P, P, P]
     lib.chi0_build_sigma_i.argtypes = [P, I, I, I, P, I, P, I]
+    lib.chi0_set_pole_grouping.argtypes = [P, D]
+    lib.chi0_set_double_grid.argtypes = [P, I, P]
     lib.chi0_ppa_eval.argtypes = [P, P, I, P, I, D, P, P]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy", "chi0_batch_destroy"):
@@ -331,6 +333,18 @@ class Chi0:
         p, dev = _ptr(out)
         self._check(_lib.chi0_invert_eps(self.h, int(iq), p, dev))
         return out
+
+    def set_pole_grouping(self, eps_thresh):
+        """chi0_set_pole_grouping: poles within eps_thresh (Ha) share one frequency factor; 0 = off."""
+        self._check(_lib.chi0_set_pole_grouping(self.h, float(eps_thresh)))
+
+    def set_double_grid(self, eps_dense):
+        """chi0_set_double_grid: eps_dense [nk][nd][nbands] (Ha), or None to switch it off."""
+        if eps_dense is None:
+            self._check(_lib.chi0_set_double_grid(self.h, 0, None))
+            return
+        e = np.ascontiguousarray(eps_dense, dtype=np.float64)
+        self._check(_lib.chi0_set_double_grid(self.h, int(e.shape[1]), e.ctypes.data))
 
     def build_sigma_i(self, iq, qp_lo, qp_hi, eps_inv, out):
         """chi0_build_sigma_i: the self-energy kernel I of Eq. (I_c) from eps~^-1

@@ -594,6 +594,40 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
     CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
   }
   c->plan_chi_iq = -1;
+  // degenerate-pole grouping (Appendix B): sort the contributing poles by
+  // energy (stable in the transition order), open a group at the smallest
+  // pole not yet taken and give it every following pole within grp_thresh;
+  // each transition then uses its representative's pole energy
+  if (c->grp_thresh > 0.0 && c->nt > 0) {
+    const int64_t nt = c->nt;
+    const int nb = c->nb;
+    std::vector<double> d(nt);
+    std::vector<int64_t> order;
+    order.reserve(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+      const int m = (int)(t % c->Nm);
+      const int64_t r = t / c->Nm;
+      const int n = c->n_lo + (int)(r % c->Nn);
+      const int ik = (int)(r / c->Nn), ikp = c->h_kq[ik];
+      d[t] = c->h_eps[(size_t)ikp * nb + m] - c->h_eps[(size_t)ik * nb + n];
+      if (c->h_occ[(size_t)ikp * nb + m] - c->h_occ[(size_t)ik * nb + n] > c->cfg.occ_drop_tol) order.push_back(t);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return d[a] < d[b]; });
+    std::vector<double> dp(d);   // transitions without weight keep their own energy
+    for (size_t i = 0; i < order.size();) {
+      const double dr = d[order[i]];
+      size_t j = i;
+      do {
+        dp[order[j]] = dr;
+        ++j;
+      } while (j < order.size() && d[order[j]] - dr < c->grp_thresh);
+      i = j;
+    }
+    chi0_status s0 = ensure(c, c->d_dpole, (size_t)nt * 8, "pole energies");
+    if (s0 != CHI0_OK) return s0;
+    CK(cudaMemcpyAsync(c->d_dpole.p, dp.data(), (size_t)nt * 8, cudaMemcpyHostToDevice, c->st), "poles H2D");
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  }
   if (c->nt > 0) {
     if ((s = ensure(c, c->d_w, (size_t)c->nt * nw * 8, "weights")) != CHI0_OK) return s;
     if ((s = ensure(c, c->d_omim, (size_t)nw * 8, "frequencies")) != CHI0_OK) return s;
@@ -638,8 +672,10 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
     cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
                                          (const double*)c->d_eps.p, (const double*)c->d_occ.p,
                                          (const double*)c->d_omim.p, (const int*)c->d_vkind.p, nw, c->cfg.eta,
-                                         pref, c->cfg.occ_drop_tol, c->bg_on, c->bg_eps, (double*)c->d_w.p,
-                                         c->st);
+                                         pref, c->cfg.occ_drop_tol, c->bg_on, c->bg_eps,
+                                         c->grp_thresh > 0.0 ? (const double*)c->d_dpole.p : nullptr,
+                                         c->dg_nd > 0 ? (const double*)c->d_epsd.p : nullptr, c->dg_nd,
+                                         (double*)c->d_w.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
     chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
@@ -1218,6 +1254,36 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
   return CHI0_OK;
 }
 
+chi0_status chi0_set_pole_grouping(chi0_ctx* c, double eps_thresh) {
+  if (!c) return CHI0_EINVAL;
+  if (!std::isfinite(eps_thresh) || eps_thresh < 0.0)
+    return fail(c, CHI0_EINVAL, "degeneracy threshold must be finite and >= 0");
+  if (eps_thresh > 0.0 && c->dg_nd > 0)
+    return fail(c, CHI0_EINVAL, "the double grid is set: pole grouping and the double grid exclude each other");
+  c->grp_thresh = eps_thresh;
+  return CHI0_OK;
+}
+
+chi0_status chi0_set_double_grid(chi0_ctx* c, int nd, const double* eps_dense) {
+  if (!c) return CHI0_EINVAL;
+  if (nd < 0 || nd > 4096 || (nd > 0 && !eps_dense)) return fail(c, CHI0_EINVAL, "nd out of range or NULL energies");
+  if (nd > 0 && c->grp_thresh > 0.0)
+    return fail(c, CHI0_EINVAL, "pole grouping is set: pole grouping and the double grid exclude each other");
+  if (nd == 0) {
+    c->dg_nd = 0;
+    return CHI0_OK;
+  }
+  const size_t n = (size_t)c->nk * nd * c->nb;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(eps_dense[i])) return fail(c, CHI0_EINVAL, "dense-grid energy %zu not finite", i);
+  chi0_status s = ensure(c, c->d_epsd, n * 8, "dense-grid energies");
+  if (s != CHI0_OK) return s;
+  CK(cudaMemcpyAsync(c->d_epsd.p, eps_dense, n * 8, cudaMemcpyHostToDevice, c->st), "dense energies H2D");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  c->dg_nd = nd;
+  return CHI0_OK;
+}
+
 chi0_status chi0_get_response_gvectors(chi0_ctx* c, int iq, int32_t* out) {
   if (!c) return CHI0_EINVAL;
   if (iq < 0 || iq >= c->cfg.nq || !out) return fail(c, CHI0_EINVAL, "bad iq or NULL out");
@@ -1336,7 +1402,7 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
                     &c->d_termq, &c->d_termw, &c->d_termc, &c->d_bgd, &c->d_bgperm, &c->d_bgkq,
                     &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx, &c->d_sigR, &c->d_sigWd,
-                    &c->d_sigY, &c->d_sigI, &c->d_sigRT};
+                    &c->d_sigY, &c->d_sigI, &c->d_sigRT, &c->d_dpole, &c->d_epsd};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)

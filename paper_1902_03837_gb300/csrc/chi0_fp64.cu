@@ -38,6 +38,7 @@ __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_
                           const double* __restrict__ eps, const double* __restrict__ occ,
                           const double* __restrict__ omega_im, const int* __restrict__ vkind, int nw,
                           double eta, double pref, double occ_tol, int bg, double eps_bar,
+                          const double* __restrict__ dpole, const double* __restrict__ epsd, int nd,
                           double* __restrict__ w) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,7 +58,21 @@ __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_
     // real frequency omega_im[iw] with broadening eta
     const int kind = vkind ? vkind[iw] : 0;
     double v = 0.0;
-    if (df > occ_tol) v = pref * df * pole_weight(kind, omega_im[iw], eta, d);
+    if (df > occ_tol) {
+      double f;
+      if (dpole) {
+        f = pole_weight(kind, omega_im[iw], eta, dpole[t]);
+      } else if (nd > 0) {
+        f = 0.0;
+        for (int j = 0; j < nd; ++j)
+          f += pole_weight(kind, omega_im[iw], eta,
+                           epsd[((size_t)ikp * nd + j) * nb + m] - epsd[((size_t)ik * nd + j) * nb + n]);
+        f /= nd;
+      } else {
+        f = pole_weight(kind, omega_im[iw], eta, d);
+      }
+      v = pref * df * f;
+    }
     if (bg && fm > occ_tol) v -= pref * fm * pole_weight(kind, omega_im[iw], eta, dbar);
     w[(size_t)iw * nt + t] = v;
   }
@@ -163,12 +178,13 @@ __global__ void k_chi0_reduce(const double2* __restrict__ part, int nchunks, int
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
                            const double* eps, const double* occ, const double* omega_im,
                            const int* vkind, int nw, double eta, double pref,
-                           double occ_tol, int bg, double eps_bar, double* w, cudaStream_t s) {
+                           double occ_tol, int bg, double eps_bar, const double* dpole, const double* epsd,
+                           int nd, double* w, cudaStream_t s) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   if (nt == 0) return cudaSuccess;
   const int64_t blocks = (nt + 255) / 256;
   k_weights<<<(unsigned)blocks, 256, 0, s>>>(nk, n_lo, Nn, Nm, nb, kq, eps, occ, omega_im, vkind, nw, eta,
-                                            pref, occ_tol, bg, eps_bar, w);
+                                            pref, occ_tol, bg, eps_bar, dpole, epsd, nd, w);
   return cudaGetLastError();
 }
 

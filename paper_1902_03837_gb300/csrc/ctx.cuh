@@ -69,6 +69,11 @@ struct chi0_ctx {
   std::vector<RhoGeom> bg_geom;        // rho geometry of each chunk of the difference set
   chi0::BgChunks bg_ch{};
   DevBuf d_bgd, d_bgperm, d_bgkq, d_bgg0, d_bgrd, d_bgw, d_bgP, d_bgidx;
+  // degenerate-pole grouping (Appendix B) and the double-grid frequency factor
+  double grp_thresh = 0.0;             // Ha; 0: every pole its own factor
+  DevBuf d_dpole;                      // [nt] pole energy of each transition's group representative
+  int dg_nd = 0;                       // dense points per k; 0: off
+  DevBuf d_epsd;                       // [nk][dg_nd][nb] dense-grid energies
   // self-energy kernel I (sigma.cu; its tensor-core operands in tc.cu):
   // rho of the quasiparticle window n in [qp_lo, qp_lo + nqp) at k and every
   // band m at k - q, W^delta and Y = W^delta conj(rho) per frequency

@@ -97,10 +97,16 @@ cudaError_t launch_rho_batch(const RhoTask<T, TOUT>* tasks_dev, int ntasks, int6
 // frequency list: kind 0 an imaginary-axis frequency i omega_im (real
 // weights); kinds 1 and 2 the real and imaginary parts of the complex weights
 // at the real frequency omega_im.
+// The frequency factor takes the pole energy d = eps_{m,k-q} - eps_{n,k}
+// unless dpole (one pole energy per transition: its degenerate group's
+// representative, Appendix B) or epsd (nd dense-grid energies per k and band,
+// [k][j][band]: the factor becomes its mean over the nd dense transitions) is
+// given.
 cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_t* kq,
                            const double* eps, const double* occ, const double* omega_im,
                            const int* vkind, int nw, double eta, double pref,
-                           double occ_tol, int bg, double eps_bar, double* w, cudaStream_t s);
+                           double occ_tol, int bg, double eps_bar, const double* dpole, const double* epsd,
+                           int nd, double* w, cudaStream_t s);
 // chi[iw] = H[vr[iw]] + i H[vi[iw]] (vi[iw] < 0: chi[iw] = H[vr[iw]])
 cudaError_t launch_combine_freq(const double2* H, const int* vr, const int* vi, int ng, int nw, double2* chi,
                                 cudaStream_t s);
