@@ -406,8 +406,10 @@ def run_ours(args, rank, world, dist):
         mpad = -(-2 * ng // 128) * 128
         kpad = -(-nt // 64) * 64
         nT = mpad // 128
-        ncontract = nw * (2 if args.real_axis else 1)  # a real frequency is two Hermitian contractions
-        issued = 3 * 2 * 128 * 128 * (nT * (nT + 1) // 2) * kpad * ncontract
+        # an imaginary frequency is one Hermitian contraction (lower-triangle
+        # tiles), a real one one contraction with complex weights (every tile)
+        tiles = nT * nT if args.real_axis else nT * (nT + 1) // 2
+        issued = 3 * 2 * 128 * 128 * tiles * kpad * nw
         extra = {"issued_tflops": issued / (per_step_ms[dom] * 1e-3) / 1e12,
                  "issued_frac": issued / (per_step_ms[dom] * 1e-3) / 1e12 / peak}
     elif bound == "fp64":

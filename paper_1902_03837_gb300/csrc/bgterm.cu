@@ -41,8 +41,10 @@ k_bg_sum(const TOUT* __restrict__ rd, const BgChunks ch, const double* __restric
 
 // chi[iw][i][j] += v, chi[iw][j][i] += conj(v) for i >= j, with
 // v = (P[d_ij] + conj(P[d_ji])) / 2 (exactly Hermitian; real on the diagonal)
+// imag = 1 adds i times the Hermitised term (the imaginary parts of complex
+// weights, added to a full complex chi0 of a real-axis frequency)
 __global__ void k_bg_apply(const double2* __restrict__ P, const int32_t* __restrict__ didx, int ng, int nd,
-                           double2* __restrict__ chi) {
+                           double2* __restrict__ chi, int imag) {
   const int iw = blockIdx.y;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
@@ -53,11 +55,14 @@ __global__ void k_bg_apply(const double2* __restrict__ P, const int32_t* __restr
   double vx = 0.5 * (a.x + b.x), vy = 0.5 * (a.y - b.y);
   double2* cw = chi + (size_t)iw * ng * ng;
   if (i == j) vy = 0.0;
+  // lower entry += v, upper entry += conj(v); times i when imag
+  const double2 lo = imag ? make_double2(-vy, vx) : make_double2(vx, vy);
+  const double2 up = imag ? make_double2(vy, vx) : make_double2(vx, -vy);
   double2 x = cw[(size_t)i * ng + j];
-  cw[(size_t)i * ng + j] = make_double2(x.x + vx, x.y + vy);
+  cw[(size_t)i * ng + j] = make_double2(x.x + lo.x, x.y + lo.y);
   if (i != j) {
     x = cw[(size_t)j * ng + i];
-    cw[(size_t)j * ng + i] = make_double2(x.x + vx, x.y - vy);
+    cw[(size_t)j * ng + i] = make_double2(x.x + up.x, x.y + up.y);
   }
 }
 
@@ -72,10 +77,10 @@ cudaError_t launch_bg_sum(const TOUT* rd, const BgChunks& ch, const double* wbar
 }
 
 cudaError_t launch_bg_apply(const double2* P, const int32_t* didx, int ng, int nd, int nw, double2* chi,
-                            cudaStream_t s) {
+                            cudaStream_t s, int imag) {
   if (ng <= 0 || nw <= 0) return cudaSuccess;
   const int64_t n = (int64_t)ng * ng;
-  k_bg_apply<<<dim3((unsigned)((n + 255) / 256), (unsigned)nw), 256, 0, s>>>(P, didx, ng, nd, chi);
+  k_bg_apply<<<dim3((unsigned)((n + 255) / 256), (unsigned)nw), 256, 0, s>>>(P, didx, ng, nd, chi, imag);
   return cudaGetLastError();
 }
 

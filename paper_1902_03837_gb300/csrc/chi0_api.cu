@@ -587,7 +587,11 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
     if ((s = ensure(c, c->d_vr, (size_t)nw0 * 4, "frequency map")) != CHI0_OK) return s;
     if ((s = ensure(c, c->d_vi, (size_t)nw0 * 4, "frequency map")) != CHI0_OK) return s;
     CK(cudaMemcpyAsync(c->d_vr.p, c->h_vr.data(), (size_t)nw0 * 4, cudaMemcpyHostToDevice, c->st), "map H2D");
-    CK(cudaMemcpyAsync(c->d_vi.p, c->h_vi.data(), (size_t)nw0 * 4, cudaMemcpyHostToDevice, c->st), "map H2D");
+    // the mixed form contracts a real frequency once with its complex weights
+    // (chi0 at its first entry): the combine then only copies it
+    c->h_vi_dev = c->h_vi;
+    if (!c->fp64) std::fill(c->h_vi_dev.begin(), c->h_vi_dev.end(), -1);
+    CK(cudaMemcpyAsync(c->d_vi.p, c->h_vi_dev.data(), (size_t)nw0 * 4, cudaMemcpyHostToDevice, c->st), "map H2D");
   }
   if (!c->d_err.p) {
     if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
@@ -707,7 +711,7 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
     } else {
       s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, c->nt, ng, nw, chiv,
                           c->term_params ? nullptr : ev_freq, c->term_params ? nullptr : ev_prep,
-                          c->bg_on ? &bga : nullptr);
+                          c->bg_on ? &bga : nullptr, c->has_real ? c->h_vkind.data() : nullptr);
       if (s != CHI0_OK) return s;
     }
     if (c->has_real && !defer_combine) {

@@ -60,6 +60,8 @@ struct chi0_ctx {
   bool has_real = false;
   std::vector<double> h_vval;            // [nwv] frequency value (imaginary part, or the real frequency)
   std::vector<int> h_vkind, h_vr, h_vi;  // [nwv] kind 0/1/2; [nw] entries of frequency iw (vi < 0: none)
+  std::vector<int> h_vi_dev;             // the vi map as uploaded (all -1 in the mixed form: chi0 of a
+                                         // real frequency comes whole from one complex contraction)
   DevBuf d_vkind, d_vr, d_vi, d_chiv;
   // Bruneval-Gonze extrapolar correction (bgterm.cu, plan in chi0_api.cu)
   int bg_on = 0;
@@ -117,9 +119,13 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw);
 // ev_freq (optional, [nw]): event w is recorded once chi of frequency w is final;
 // ev_prep (optional, [nw]): event w once the operand of frequency w is split
 // bg (optional): the extrapolar term added to each frequency after its reduction
+// vkind (optional, host, [nw]): kinds of the frequency list; an entry of kind 1
+// followed by one of kind 2 is contracted once with the complex weights
+// w[v] + i w[v + 1] over the full tile grid, its chi0 written at entry v
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq = nullptr,
-                      const cudaEvent_t* ev_prep = nullptr, const chi0::BgApply* bg = nullptr);
+                      const cudaEvent_t* ev_prep = nullptr, const chi0::BgApply* bg = nullptr,
+                      const int* vkind = nullptr);
 void tc_release(chi0_ctx* c);
 // self-energy kernel I (Eq. I_c) on the tensor cores: Y(i, t) = sum_j
 // W^d_ij conj(rho_t(j)) for T transitions of the quasiparticle window, written

@@ -126,7 +126,7 @@ template <typename TOUT>
 cudaError_t launch_bg_sum(const TOUT* rd, const BgChunks& ch, const double* wbar, int64_t ntd, int nd,
                           int nw, double2* P, cudaStream_t s);
 cudaError_t launch_bg_apply(const double2* P, const int32_t* didx, int ng, int nd, int nw, double2* chi,
-                            cudaStream_t s);
+                            cudaStream_t s, int imag = 0);
 // The extrapolar term of every frequency, applied by the contraction right
 // after its own reduction of that frequency (before its per-frequency event).
 struct BgApply {

@@ -426,27 +426,32 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
 constexpr int kPT = 64;  // transitions per tile (= one k-block)
 constexpr int kPI = 32;  // complex G per tile
 
-// Up to kPrepGroup frequencies are split in one pass, so that R is read once
+// Up to kPrepGroup operands are split in one pass, so that R is read once
 // for all of them (the split is bound by HBM traffic: R in, hi/lo out).
+// Operand g is R scaled by the weights wr[g][t] (NULL: unit weights), or, with
+// wi[g] given, by the complex weights wr[g][t] + i wi[g][t] (a real-axis
+// frequency: A = w rho with rows Re = wr x - wi y, Im = wr y + wi x).
 constexpr int kPrepGroup = 8;
 struct PrepOut {
   __nv_bfloat16* hi[kPrepGroup];
   __nv_bfloat16* lo[kPrepGroup];
+  const double* wr[kPrepGroup];
+  const double* wi[kPrepGroup];
 };
 
-// w: NULL (unit weights) or the weights of ngrp consecutive frequencies, w[g * nt + t]
 __global__ void __launch_bounds__(256)
-k_prep(const float2* __restrict__ R, const double* __restrict__ w, int ngrp, int64_t nt, int ng,
-       int mpad, const __grid_constant__ PrepOut out) {
+k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, const __grid_constant__ PrepOut out) {
   __shared__ float tile[2 * kPI][kPT + 1];
-  __shared__ float ws[kPrepGroup][kPT];  // weights converted once per transition (FP64 is slow here)
+  __shared__ float ws[kPrepGroup][kPT];   // weights converted once per transition (FP64 is slow here)
+  __shared__ float wsi[kPrepGroup][kPT];  // imaginary parts of complex weights
   const int64_t kb = blockIdx.x;
   const int64_t t0 = kb * kPT;
   const int i0 = blockIdx.y * kPI;
   for (int e = threadIdx.x; e < ngrp * kPT; e += 256) {
     const int g = e / kPT, tl = e % kPT;
     const int64_t t = t0 + tl;
-    ws[g][tl] = (w && t < nt) ? (float)w[(size_t)g * nt + t] : 1.f;
+    ws[g][tl] = (out.wr[g] && t < nt) ? (float)out.wr[g][t] : 1.f;
+    wsi[g][tl] = (out.wi[g] && t < nt) ? (float)out.wi[g][t] : 0.f;
   }
   for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
     const int tl = e / kPI, il = e % kPI;
@@ -461,9 +466,26 @@ k_prep(const float2* __restrict__ R, const double* __restrict__ w, int ngrp, int
   for (int g = 0; g < ngrp; ++g) {
     __nv_bfloat16* __restrict__ hi = out.hi[g];
     __nv_bfloat16* __restrict__ lo = out.lo[g];
+    const bool cplx = out.wi[g] != nullptr;
     for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
       const int ml = e / (kPT / 2), tp = e % (kPT / 2);
-      const float x0 = tile[ml][2 * tp] * ws[g][2 * tp], x1 = tile[ml][2 * tp + 1] * ws[g][2 * tp + 1];
+      float x0, x1;
+      if (cplx) {
+        // row 2 i: Re(w rho) = wr x - wi y; row 2 i + 1: Im(w rho) = wr y + wi x
+        const int mr = ml & ~1;
+        const float a0 = tile[mr][2 * tp], b0 = tile[mr + 1][2 * tp];
+        const float a1 = tile[mr][2 * tp + 1], b1 = tile[mr + 1][2 * tp + 1];
+        if (ml & 1) {
+          x0 = fmaf(ws[g][2 * tp], b0, wsi[g][2 * tp] * a0);
+          x1 = fmaf(ws[g][2 * tp + 1], b1, wsi[g][2 * tp + 1] * a1);
+        } else {
+          x0 = fmaf(ws[g][2 * tp], a0, -wsi[g][2 * tp] * b0);
+          x1 = fmaf(ws[g][2 * tp + 1], a1, -wsi[g][2 * tp + 1] * b1);
+        }
+      } else {
+        x0 = tile[ml][2 * tp] * ws[g][2 * tp];
+        x1 = tile[ml][2 * tp + 1] * ws[g][2 * tp + 1];
+      }
       const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
       const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
       const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
@@ -494,11 +516,30 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
   if (i != j) chi[(size_t)j * ng + i] = make_double2(sx, -sy);
 }
 
+// chi[i][j] = sum over chunks of the partials of the full tile grid (A rows i,
+// B rows j: tile (i / 64) + (j / 64) nT), every entry (no Hermitian symmetry).
+__global__ void k_tc_reduce_full(const double2* __restrict__ part, int nchunks, int ntiles, int nT, int ng,
+                                 double2* __restrict__ chi) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ng * ng) return;
+  const int i = (int)(e / ng), j = (int)(e % ng);
+  const int tile = i / (kBM / 2) + (j / (kBN / 2)) * nT;
+  const size_t off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  double sx = 0.0, sy = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const double2 v = part[((size_t)c * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
+    sx += v.x;
+    sy += v.y;
+  }
+  chi[e] = make_double2(sx, sy);
+}
+
 struct TcState {
   DevBuf ah[kPrepGroup], al[kPrepGroup], bh, bl, part;
   CUtensorMap m_ah[kPrepGroup], m_al[kPrepGroup], m_bh, m_bl;
   int64_t kpad = 0;
   int mpad = 0, ntiles = 0, total_kb = 0, kbpc = 0, nchunks = 0;
+  int ntiles_f = 0, kbpc_f = 0, nchunks_f = 0;   // full tile grid (complex weights)
   int group = 1;  // frequencies per operand-split pass (A buffers in use)
   int nsm = 1;    // persistent contraction grid
 };
@@ -548,30 +589,37 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     cudaGetLastError();
   }
   t.nsm = nsm;
-  int nsplit = 1;
-  double best = 1e30;
-  for (int sp = 1; sp <= 64; ++sp) {
-    const int kbps = (t.total_kb + sp - 1) / sp;
-    if (sp > 1 && kbps < 8 * kSubKB) break;  // keep every CTA busy for a while
-    const int ctas = t.ntiles * sp;
-    const int waves = (ctas + nsm - 1) / nsm;
-    // time ~ waves * work per CTA; prefer fewer partials on ties
-    const double cost = (double)waves * kbps + 4.0 * sp;
-    if (cost < best) {
-      best = cost;
-      nsplit = sp;
+  auto choose_split = [&](int ntiles, int& kbpc, int& nchunks) {
+    int nsplit = 1;
+    double best = 1e30;
+    for (int sp = 1; sp <= 64; ++sp) {
+      const int kbps = (t.total_kb + sp - 1) / sp;
+      if (sp > 1 && kbps < 8 * kSubKB) break;  // keep every CTA busy for a while
+      const int ctas = ntiles * sp;
+      const int waves = (ctas + nsm - 1) / nsm;
+      // time ~ waves * work per CTA; prefer fewer partials on ties
+      const double cost = (double)waves * kbps + 4.0 * sp;
+      if (cost < best) {
+        best = cost;
+        nsplit = sp;
+      }
     }
-  }
-  t.kbpc = (t.total_kb + nsplit - 1) / nsplit;
-  t.nchunks = (t.total_kb + t.kbpc - 1) / t.kbpc;
+    kbpc = (t.total_kb + nsplit - 1) / nsplit;
+    nchunks = (t.total_kb + kbpc - 1) / kbpc;
+  };
+  choose_split(t.ntiles, t.kbpc, t.nchunks);
+  // the full tile grid of the complex contraction of a real-axis frequency
+  t.ntiles_f = nT * nT;
+  choose_split(t.ntiles_f, t.kbpc_f, t.nchunks_f);
   if (t.kpad / kPT > 0x7fffffff / t.mpad)
     return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
   const size_t opb = (size_t)t.mpad * t.kpad * 2;
   chi0_status s;
   if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
-  if ((s = ctx_ensure(c, t.part, (size_t)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16,
-                      "chunk partials")) != CHI0_OK)
+  const size_t nparts = std::max((size_t)t.nchunks * t.ntiles,
+                                  c->has_real ? (size_t)t.nchunks_f * t.ntiles_f : (size_t)0);
+  if ((s = ctx_ensure(c, t.part, nparts * (kBM / 2) * (kBN / 2) * 16, "chunk partials")) != CHI0_OK)
     return s;
   // A buffers for up to kPrepGroup frequencies, as far as half of the free
   // device memory allows (one pair is always needed)
@@ -610,62 +658,117 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tc_reduce, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_reduce_full, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
 }
 
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep,
-                      const BgApply* bg) {
+                      const BgApply* bg, const int* vkind) {
   if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "tensor-core contraction not planned");
   TcState& t = *static_cast<TcState*>(c->tc);
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
   const int64_t n2 = (int64_t)ng * ng;
+  const int nT = t.mpad / kBM;
   // B = rho (frequency independent)
   PrepOut ob{};
   ob.hi[0] = (__nv_bfloat16*)t.bh.p;
   ob.lo[0] = (__nv_bfloat16*)t.bl.p;
   stage_begin(c, CHI0_STAGE_WEIGHTS);
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, nullptr, 1, nt, ng, t.mpad, ob);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, 1, nt, ng, t.mpad, ob);
   stage_end(c, CHI0_STAGE_WEIGHTS, 1);
-  PrepOut oa{};
-  for (int g = 0; g < t.group; ++g) {
-    oa.hi[g] = (__nv_bfloat16*)t.ah[g].p;
-    oa.lo[g] = (__nv_bfloat16*)t.al[g].p;
+  // jobs: an entry of the frequency list with real weights is one Hermitian
+  // contraction (lower-triangle tiles); a real-axis frequency (entries of
+  // kinds 1 and 2: the real and imaginary parts of its complex weights) is one
+  // contraction with complex weights over the full tile grid, whose result is
+  // chi0 of that frequency, written at its first entry
+  struct Job {
+    int v;
+    bool cplx;
+  };
+  std::vector<Job> jobs;
+  for (int v = 0; v < nw; ++v) {
+    const bool cplx = vkind && vkind[v] == 1 && v + 1 < nw && vkind[v + 1] == 2;
+    jobs.push_back({v, cplx});
+    if (cplx) ++v;
   }
-  const int nunits = t.ntiles * t.nchunks;
+  const int nunits = t.ntiles * t.nchunks, nunits_f = t.ntiles_f * t.nchunks_f;
   const unsigned hgrid = (unsigned)std::min(nunits, std::max(1, t.nsm));
-  int passes = 0;
-  for (int w0 = 0; w0 < nw; w0 += t.group, ++passes) {
-    const int gw = std::min(t.group, nw - w0);
+  const unsigned hgrid_f = (unsigned)std::min(nunits_f, std::max(1, t.nsm));
+  int passes = 0, nherm = 0, nfull = 0;
+  for (size_t j0 = 0; j0 < jobs.size(); j0 += t.group, ++passes) {
+    const int gw = (int)std::min<size_t>(t.group, jobs.size() - j0);
+    PrepOut oa{};
+    for (int g = 0; g < gw; ++g) {
+      const Job& jb = jobs[j0 + g];
+      oa.hi[g] = (__nv_bfloat16*)t.ah[g].p;
+      oa.lo[g] = (__nv_bfloat16*)t.al[g].p;
+      oa.wr[g] = w + (size_t)jb.v * nt;
+      oa.wi[g] = jb.cplx ? w + (size_t)(jb.v + 1) * nt : nullptr;
+    }
     stage_begin(c, CHI0_STAGE_WEIGHTS);
-    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, w + (size_t)w0 * nt, gw, nt, ng, t.mpad, oa);
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, gw, nt, ng, t.mpad, oa);
     stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     if (ev_prep)
-      for (int g = 0; g < gw; ++g) cudaEventRecord(ev_prep[w0 + g], c->st);
+      for (int g = 0; g < gw; ++g) {
+        cudaEventRecord(ev_prep[jobs[j0 + g].v], c->st);
+        if (jobs[j0 + g].cplx) cudaEventRecord(ev_prep[jobs[j0 + g].v + 1], c->st);
+      }
     for (int g = 0; g < gw; ++g) {
-      const int iw = w0 + g;
+      const Job& jb = jobs[j0 + g];
+      double2* out = chi + (size_t)jb.v * n2;
       stage_begin(c, CHI0_STAGE_CONTRACT);
-      k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
-          t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
-          nunits, (int*)c->d_err.p, 0, t.mpad, 0);
+      if (jb.cplx) {
+        k_herk_bf16x3<<<hgrid_f, kThreads, kSmemBytes, c->st>>>(
+            t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
+            nunits_f, (int*)c->d_err.p, nT, t.mpad, 0);
+        ++nfull;
+      } else {
+        k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
+            t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
+            nunits, (int*)c->d_err.p, 0, t.mpad, 0);
+        ++nherm;
+      }
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
       stage_begin(c, CHI0_STAGE_REDUCE);
-      k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
-          (const double2*)t.part.p, t.nchunks, t.ntiles, ng, chi + (size_t)iw * n2);
-      if (bg) launch_bg_apply(bg->P + (size_t)iw * bg->nd, bg->didx, ng, bg->nd, 1, chi + (size_t)iw * n2, c->st);
-      stage_end(c, CHI0_STAGE_REDUCE, bg ? 2 : 1);
-      if (ev_freq) cudaEventRecord(ev_freq[iw], c->st);
+      if (jb.cplx)
+        k_tc_reduce_full<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks_f,
+                                                                           t.ntiles_f, nT, ng, out);
+      else
+        k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks, t.ntiles,
+                                                                      ng, out);
+      int nk = 1;
+      if (bg) {
+        launch_bg_apply(bg->P + (size_t)jb.v * bg->nd, bg->didx, ng, bg->nd, 1, out, c->st, 0);
+        ++nk;
+        if (jb.cplx) {   // + i (Hermitised P of the imaginary parts)
+          launch_bg_apply(bg->P + (size_t)(jb.v + 1) * bg->nd, bg->didx, ng, bg->nd, 1, out, c->st, 1);
+          ++nk;
+        }
+      }
+      stage_end(c, CHI0_STAGE_REDUCE, nk);
+      if (ev_freq) {
+        cudaEventRecord(ev_freq[jb.v], c->st);
+        if (jb.cplx) cudaEventRecord(ev_freq[jb.v + 1], c->st);
+      }
     }
   }
-  // operand split: R read once per pass, hi/lo written (B once, A per frequency)
-  c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(passes + 1) * nt * ng * 8 + (double)(nw + 1) * 4.0 * t.mpad * t.kpad;
+  const double tile_bytes = (double)(kBM / 2) * (kBN / 2) * 16;
+  // operand split: R read once per pass, hi/lo written (B once, A per job)
+  c->stage[CHI0_STAGE_WEIGHTS].bytes +=
+      (double)(passes + 1) * nt * ng * 8 + (double)(jobs.size() + 1) * 4.0 * t.mpad * t.kpad;
   // contraction: each launch streams A and B (hi and lo) once and writes its chunk partials
   c->stage[CHI0_STAGE_CONTRACT].bytes =
-      (double)nw * (8.0 * t.mpad * t.kpad + (double)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16);
-  c->stage[CHI0_STAGE_REDUCE].bytes = (double)nw * ((double)t.nchunks * t.ntiles * (kBM / 2) * (kBN / 2) * 16 + n2 * 16);
-  // tensor-core work actually issued: 3 BF16 products over the lower-triangle tiles
-  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)t.ntiles * (double)t.kpad * nw;
+      (double)(nherm + nfull) * 8.0 * t.mpad * t.kpad +
+      ((double)nherm * t.nchunks * t.ntiles + (double)nfull * t.nchunks_f * t.ntiles_f) * tile_bytes;
+  c->stage[CHI0_STAGE_REDUCE].bytes =
+      ((double)nherm * t.nchunks * t.ntiles + (double)nfull * t.nchunks_f * t.ntiles_f) * tile_bytes +
+      (double)(nherm + nfull) * n2 * 16;
+  // tensor-core work actually issued: 3 BF16 products over the tiles of each launch
+  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)t.kpad * ((double)t.ntiles * nherm + (double)t.ntiles_f * nfull);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
