@@ -126,7 +126,7 @@ struct DotSum {
 // layout, both coalesced across the warp), A partners per pass.  Products in
 // the element type of rho, summed kDotUnroll at a time into a DotSum.
 template <typename TR, typename TY, int A>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(TR) == 8 && A == 4) ? 3 : 1)
 k_sig_dot(const TR* __restrict__ RT, const TY* __restrict__ Y, int ng, int64_t T, int nqp, int nI, double pref,
           double2* __restrict__ out) {
   using F = decltype(TR::x);
@@ -147,10 +147,32 @@ k_sig_dot(const TR* __restrict__ RT, const TY* __restrict__ Y, int ng, int64_t T
         F cx[A], cy[A];
 #pragma unroll
         for (int q = 0; q < A; ++q) cx[q] = cy[q] = 0;
+        if (i0 + 4 * (kDotUnroll - 1) < ng) {
+          // a full block of kDotUnroll values of i: no guards, so that every
+          // load of the block can be in flight at once
+          TY yv[kDotUnroll];
 #pragma unroll
-        for (int r = 0; r < kDotUnroll; ++r) {
-          const int i = i0 + 4 * r;
-          if (i < ng) {
+          for (int r = 0; r < kDotUnroll; ++r) {
+            const int i = i0 + 4 * r;
+            yv[r] = Ycol[(size_t)(i >> 6) * 4096 + (size_t)(i & 63) * 64];
+          }
+#pragma unroll
+          for (int r = 0; r < kDotUnroll; ++r) {
+            const int i = i0 + 4 * r;
+            const size_t ro = (size_t)(i >> 6) * 4096 + (size_t)(i & 63) * 64;
+            const F yx = (F)yv[r].x, yy = (F)yv[r].y;
+#pragma unroll
+            for (int q = 0; q < A; ++q)
+              if (a0 + q < nqp) {
+                const TR v = col[q][ro];
+                cx[q] += v.x * yx - v.y * yy;
+                cy[q] += v.x * yy + v.y * yx;
+              }
+          }
+        } else {
+          for (int r = 0; r < kDotUnroll; ++r) {
+            const int i = i0 + 4 * r;
+            if (i >= ng) break;
             const size_t ro = (size_t)(i >> 6) * 4096 + (size_t)(i & 63) * 64;
             const TY yd = Ycol[ro];
             const F yx = (F)yd.x, yy = (F)yd.y;
