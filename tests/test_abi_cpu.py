@@ -87,6 +87,54 @@ def test_call_order_and_arguments(binding):
     c.close()
 
 
+def test_new_entry_points_reject_bad_arguments(binding):
+    """Argument and call-order checks of the plasmon-pole, self-energy,
+    grouping and double-grid entry points; all of them return before any
+    device memory is touched (the non-NULL pointers below are never read)."""
+    import ctypes
+    lib = binding._lib
+    fake = ctypes.c_void_p(16)
+    assert lib.chi0_ppa_fit(None, fake, 4, 1.0, fake, fake, None) == -1
+    assert lib.chi0_ppa_fit(fake, fake, 0, 1.0, fake, fake, None) == -1
+    assert lib.chi0_ppa_fit(fake, fake, 4, 0.0, fake, fake, None) == -1
+    assert lib.chi0_ppa_fit(fake, fake, 4, float("nan"), fake, fake, None) == -1
+    assert lib.chi0_ppa_eval(fake, fake, 4, None, 1, 0.0, fake, None) == -1      # nf > 0 needs frequencies
+    f = (ctypes.c_double * 2)(0.3, float("inf"))
+    assert lib.chi0_ppa_eval(fake, fake, 4, f, 1, 0.0, fake, None) == -1
+    assert lib.chi0_ppa_eval(fake, fake, 4, f, 1, -1.0, fake, None) == -1
+    c = _ctx(binding)
+    h = c.h
+    assert lib.chi0_build_sigma_i(h, 0, 5, 5, fake, 1, fake, 1) == -1            # empty window
+    assert lib.chi0_build_sigma_i(h, 0, 30, 33, fake, 1, fake, 1) == -1          # beyond nbands = 32
+    assert lib.chi0_build_sigma_i(h, 0, 0, 4, None, 1, fake, 1) == -1
+    assert lib.chi0_build_sigma_i(h, 0, 0, 4, fake, 0, fake, 1) == -1
+    assert lib.chi0_build_sigma_i(h, 1, 0, 4, fake, 1, fake, 1) == -1            # iq out of range
+    assert lib.chi0_build_sigma_i(h, 0, 0, 4, fake, 1, fake, 1) == -4            # compute_rho first
+    with pytest.raises(binding.Chi0Error) as ei:
+        c.set_pole_grouping(-1e-5)
+    assert ei.value.status == -1
+    with pytest.raises(binding.Chi0Error) as ei:
+        c.set_pole_grouping(float("nan"))
+    assert ei.value.status == -1
+    assert lib.chi0_set_double_grid(h, -1, None) == -1
+    assert lib.chi0_set_double_grid(h, 2, None) == -1
+    bad = np.zeros((64, 2, 32))
+    bad[3, 1, 7] = np.inf
+    with pytest.raises(binding.Chi0Error) as ei:
+        c.set_double_grid(bad)
+    assert ei.value.status == -1
+    c.set_pole_grouping(1e-5)
+    with pytest.raises(binding.Chi0Error) as ei:                               # the two exclude each other
+        c.set_double_grid(np.zeros((64, 2, 32)))
+    assert ei.value.status == -1
+    c.set_pole_grouping(0.0)
+    c.set_double_grid(None)
+    with pytest.raises(binding.Chi0Error) as ei:
+        c.set_bg_terminator(float("nan"))
+    assert ei.value.status == -1
+    c.close()
+
+
 def test_injected_allocation_failure(binding, monkeypatch):
     c = _ctx(binding)
     monkeypatch.setenv("CHI0_FAULT", "alloc")
