@@ -330,6 +330,7 @@ def run_ours(args, rank, world, dist):
         else:
             ctx.build_invert(0, out_h)   # device -> host copy of the result, synchronises
 
+    e2e_clk = None
     if args.no_e2e:
         e2e_ms = None
     else:
@@ -337,12 +338,13 @@ def run_ours(args, rank, world, dist):
         e2e_steps = max(1, min(args.steps, 3))
         barrier()
         torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        barrier()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        with ClockSampler(local) as e2e_clk:
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                e2e_step()
+            torch.cuda.synchronize(dev)
+            barrier()
+            e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
         if dist is not None:
             t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -450,7 +452,9 @@ def run_ours(args, rank, world, dist):
         "roofline": roof,
         "e2e": (None if e2e_ms is None else
                 {"value": world * flops_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}),
+                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 # the e2e steps follow the timed region: the SM clock they ran at
+                 "clocks": e2e_clk.summary() if e2e_clk is not None else None}),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
