@@ -43,6 +43,23 @@ def chi0_flops(ng, nt, nw):
     return 4.0 * ng * (ng + 1) * nt * nw
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process group):
+    the job's time is that of its slowest replica."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(world, flops_per_step, ms_per_step):
+    """Throughput of the whole job: each of the world ranks runs one replica
+    of the step (no data-path collective), in the slowest rank's time."""
+    return world * flops_per_step / (ms_per_step * 1e-3) / 1e12
+
+
 # stage -> (binding roof, unit, kernel)
 STAGE_ROOF = {"contract": ("tensor", "TFLOP/s", "k_herk_bf16x3"), "rho": ("alu", "TFLOP/s", "k_rho_pairs"),
               "wf_grid": ("alu", "TFLOP/s", "k_wf_to_mixed"), "dyson": ("fp64", "TFLOP/s", "k_gj_update"),
@@ -303,13 +320,10 @@ def run_ours(args, rank, world, dist):
     ctx.synchronize()
     st_ms, st_bytes, st_flops, l1 = ctx.get_stats()
     launches = (l1 - l0) + ppa_launches
-    if dist is not None:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
     flops_step = chi0_flops(ng, nt, nw)
-    value = world * flops_step / (ms_step * 1e-3) / 1e12
+    value = whole_job_tflops(world, flops_step, ms_step)
 
     # ---- end to end: host buffers, copies inside the timed region
     pin_gv = [torch.from_numpy(np.ascontiguousarray(s.gvec[ik, :s.npw[ik]])).pin_memory() for ik in range(s.nk)]
@@ -345,10 +359,7 @@ def run_ours(args, rank, world, dist):
             torch.cuda.synchronize(dev)
             barrier()
             e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-        if dist is not None:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     sigma_line = None
     if args.sigma:
         # the self-energy kernel I (Eq. I_c) on the real-axis eps~^-1 of this
@@ -451,7 +462,7 @@ def run_ours(args, rank, world, dist):
         "stage_ms_per_step": per_step_ms,
         "roofline": roof,
         "e2e": (None if e2e_ms is None else
-                {"value": world * flops_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                {"value": whole_job_tflops(world, flops_step, e2e_ms), "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  # the e2e steps follow the timed region: the SM clock they ran at
                  "clocks": e2e_clk.summary() if e2e_clk is not None else None}),
