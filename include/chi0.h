@@ -32,9 +32,10 @@
  *     with f_{m,k-q} - f_{n,k} <= occ_drop_tol carry zero weight;
  *   - the response G set is the ng vectors of smallest |q+G|, ties broken by
  *     ascending (Gx, Gy, Gz), |q+G|^2 compared exactly;
- *   - only Hermitian cases are supported (time-reversal-symmetric inputs and
- *     real weights: imaginary frequencies with eta = 0, or w = 0 with any eta);
- *     other frequencies return CHI0_EUNSUPPORTED.
+ *   - time-reversal-symmetric inputs only; frequencies on the imaginary axis
+ *     (real weights, Hermitian chi0) or on the real axis with eta > 0
+ *     (complex weights; chi0 and eps~ general complex matrices); other
+ *     frequencies return CHI0_EUNSUPPORTED.
  *
  * Asynchrony: every call that launches work is asynchronous on
  * config.cuda_stream (NULL = the legacy default stream).  The returned status
@@ -89,8 +90,9 @@ typedef struct {
   int nw;                 /* number of frequencies */
   const double* omega;    /* [nw][2] complex frequencies (re, im) in Ha; copied at chi0_create.
                              Either imaginary-axis (re = 0: chi0 Hermitian) or real-axis (im = 0,
-                             re > 0, and eta > 0: complex weights, chi0 = H_r + i H_i from two
-                             Hermitian contractions, eps~ inverted by general Gauss-Jordan);
+                             re > 0, and eta > 0: complex weights, chi0 = H_r + i H_i: one
+                             complex-weight contraction in the mixed form, two Hermitian ones
+                             combined in the FP64 form; eps~ inverted by general Gauss-Jordan);
                              other forms give CHI0_EUNSUPPORTED at chi0_build_chi0 */
   double eta;             /* Ha; +i*eta on both poles (retarded); 0 on the imaginary axis */
   double spin_factor;     /* f_s: 2 without spin polarisation, 1 with it */
@@ -190,8 +192,19 @@ chi0_status chi0_get_rho(chi0_ctx* ctx, void* out);
 chi0_status chi0_get_rho_rows(chi0_ctx* ctx, const int64_t* rows, int64_t nrows, void* out);
 
 /* Wait for all work queued by this context and report device-side errors
- * (CHI0_ETIMEOUT, CHI0_ENOTPD, CHI0_ECUDA). */
+ * (CHI0_ETIMEOUT, CHI0_ENOTPD, CHI0_ECUDA).  Reading an error clears the
+ * device flag, so the context stays usable. */
 chi0_status chi0_synchronize(chi0_ctx* ctx);
+
+/* Failure detection check (no counterpart in the paper): queue one kernel
+ * whose single thread waits, through the bounded wait every spin-wait of the
+ * contraction uses, on a barrier that nothing completes.  The wait gives up
+ * after about two seconds, raises the device error flag and the kernel
+ * returns; the next chi0_synchronize reports CHI0_ETIMEOUT and clears the
+ * flag.  While it runs, other contraction launches of any context sharing
+ * the flag would stop early, so call it with nothing else queued.
+ * Errors: CHI0_EINVAL, CHI0_ENOMEM, CHI0_ECUDA. */
+chi0_status chi0_check_bounded_wait(chi0_ctx* ctx);
 
 /* Stages of the path, for chi0_get_stats. */
 enum {

@@ -31,6 +31,7 @@ EXPORTS = (
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator", "chi0_set_bg_terminator",
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
     "chi0_ppa_fit", "chi0_ppa_eval", "chi0_build_sigma_i", "chi0_set_pole_grouping", "chi0_set_double_grid",
+    "chi0_check_bounded_wait",
 )
 
 
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_build_sigma_i.argtypes = [P, I, I, I, P, I, P, I]
     lib.chi0_set_pole_grouping.argtypes = [P, D]
     lib.chi0_set_double_grid.argtypes = [P, I, P]
+    lib.chi0_check_bounded_wait.argtypes = [P]
     lib.chi0_ppa_eval.argtypes = [P, P, I, P, I, D, P, P]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy", "chi0_batch_destroy"):
@@ -394,6 +396,11 @@ class Chi0:
 
     def synchronize(self):
         self._check(_lib.chi0_synchronize(self.h))
+
+    def check_bounded_wait(self):
+        """chi0_check_bounded_wait: queue a bounded wait that must give up; the
+        next synchronize raises Chi0Error with CHI0_ETIMEOUT."""
+        self._check(_lib.chi0_check_bounded_wait(self.h))
 
     def term_features(self, iq, chi_trunc, x, chi_full=None, t=None):
         """Features (and targets) of a truncated chi0 held on the device; returns the scale c."""

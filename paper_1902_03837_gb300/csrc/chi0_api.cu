@@ -1359,6 +1359,18 @@ chi0_status chi0_get_rho_rows(chi0_ctx* c, const int64_t* rows, int64_t nrows, v
   return CHI0_OK;
 }
 
+chi0_status chi0_check_bounded_wait(chi0_ctx* c) {
+  if (!c) return CHI0_EINVAL;
+  chi0_status s;
+  if (!c->d_err.p) {
+    if ((s = ensure(c, c->d_err, 16, "error flag")) != CHI0_OK) return s;
+    CK(cudaMemsetAsync(c->d_err.p, 0, 16, c->st), "clear error flag");
+  }
+  cudaError_t e = chi0::launch_wait_probe((int*)c->d_err.p, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "wait probe launch");
+  return CHI0_OK;
+}
+
 chi0_status chi0_synchronize(chi0_ctx* c) {
   if (!c) return CHI0_EINVAL;
   CK(cudaStreamSynchronize(c->st), "synchronize");

@@ -127,6 +127,8 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
                       const cudaEvent_t* ev_prep = nullptr, const chi0::BgApply* bg = nullptr,
                       const int* vkind = nullptr);
 void tc_release(chi0_ctx* c);
+// one bounded mbarrier wait that can never be satisfied (failure detection)
+cudaError_t launch_wait_probe(int* err, cudaStream_t s);
 // self-energy kernel I (Eq. I_c) on the tensor cores: Y(i, t) = sum_j
 // W^d_ij conj(rho_t(j)) for T transitions of the quasiparticle window, written
 // in FP32 as 64 x 64 complex tiles, tile (i / 64) + (t / 64) * ceil(ng / 64)

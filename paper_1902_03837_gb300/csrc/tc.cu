@@ -788,6 +788,32 @@ void tc_release(chi0_ctx* c) {
   c->tc = nullptr;
 }
 
+// ---- failure detection: the bounded wait ---------------------------------------
+// One thread waits on an mbarrier that nothing arrives on, through the same
+// bounded wait as the contraction's producer, MMA and epilogue roles: after
+// kSpinCycles it gives up, raises the device error flag (reported as
+// CHI0_ETIMEOUT by the next synchronising call) and the kernel returns.
+
+namespace {
+
+__global__ void k_wait_probe(int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(smem_u32(&bar), 0u, &abort_flag, err);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_wait_probe(int* err, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
+}
+
 // ---- self-energy kernel I (Eq. I_c) -----------------------------------------
 // Y(i, t) = sum_j W^d_ij conj(rho_t(j)) is the same complex product as the
 // chi0 contraction, C_ij = sum_K A_K(i) conj(B_K(j)), with K = G' (ng values)
