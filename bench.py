@@ -489,6 +489,101 @@ def run_ours(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_batching(args, rank, world, dist):
+    """The batching workload: 16 seeded metallic systems of different sizes
+    (one q point each), all problems in one batch (one persistent rho launch,
+    every other kernel in one CUDA graph), against the same problems one at a
+    time, and the first system in the plain FP64 form."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1902_03837_gb300 import chi0 as lib
+    from synth import make_batching_system
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    systems = [make_batching_system(s_, nq_max=1) for s_ in range(16)]
+    ctxs, outs = [], []
+    for sy in systems:
+        c = lib.Chi0.for_system(sy, precision=lib.CHI0_MIXED_BF16X3, stream=st, occ_drop_tol=1e-12)
+        c.load_system(sy)
+        ctxs.append(c)
+        outs.append(torch.empty((sy.freqs.size, sy.ng, sy.ng), dtype=torch.complex128, device=dev))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(ctxs) + 2)]
+
+    def one_at_a_time():
+        for i, c in enumerate(ctxs):
+            ev[2 * i].record(stream)
+            c.compute_rho(0)
+            c.build_invert(0, outs[i])
+            ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ctxs))]
+
+    one_at_a_time()                                  # plans every problem
+    nts = [c.get_transitions().shape[0] for c in ctxs]
+    flops = sum(chi0_flops(sy.ng, nt, sy.freqs.size) for sy, nt in zip(systems, nts))
+    seq = [one_at_a_time() for _ in range(2)]
+    seq_ms = min(sum(r) for r in seq)
+    per_problem = [min(r[i] for r in seq) for i in range(len(ctxs))]
+    batch = lib.Batch(ctxs, [0] * len(ctxs), outs, nstreams=4)
+    for _ in range(args.warmup):
+        batch.run(st)
+    torch.cuda.synchronize(dev)
+    e0, e1 = ev[-2], ev[-1]
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.run(st)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    for c in ctxs:
+        c.synchronize()
+    batch_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    width = batch.rho_width()
+    batch.close()
+    for c in ctxs:
+        c.close()
+    # the plain FP64 form of the first system, for the speedup at the same size
+    s0 = systems[0]
+    c64 = lib.Chi0.for_system(s0, precision=lib.CHI0_FP64, stream=st, occ_drop_tol=1e-12)
+    c64.load_system(s0)
+    o64 = torch.empty_like(outs[0])
+    c64.compute_rho(0)
+    c64.build_invert(0, o64)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    c64.compute_rho(0)
+    c64.build_invert(0, o64)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_ms = e0.elapsed_time(e1)
+    err0 = ((o64 - outs[0]).abs().pow(2).sum() / o64.abs().pow(2).sum()).sqrt().item()
+    c64.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "batched chi0(q,w) + eps^-1 throughput (algorithmic Hermitian TFLOP/s)",
+        "value": whole_job_tflops(world, flops, batch_ms), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)",
+        "data": "synthetic",
+        "config": {"workload": "batching: 16 metallic systems (seeds 3000-3015; a 8-14 bohr, 4x4x4 k, 64 bands, "
+                               "400-4000 PW, N_G 200-1500, 8-64 imaginary GL frequencies, Fermi-Dirac 0.05 eV), "
+                               "the first q point of each", "problems": len(ctxs), "n_transitions": nts,
+                   "ng": [sy.ng for sy in systems], "nw": [int(sy.freqs.size) for sy in systems],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "batch_ms": batch_ms, "one_at_a_time_ms": seq_ms, "speedup_vs_one_at_a_time": seq_ms / batch_ms,
+        "rho_width": width, "problem_ms": per_problem,
+        "fp64_system0_ms": fp64_ms, "mixed_system0_ms": per_problem[0],
+        "speedup_vs_fp64_system0": fp64_ms / per_problem[0], "error_vs_fp64_system0": err0,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,6 +610,8 @@ def main():
                     metavar="LO,HI", help="then time the self-energy kernel I (Eq. I_c) for the bands [LO, HI) at k "
                                           "on the real-axis eps~^-1 of --ppa or --real-axis")
     ap.add_argument("--sigma-steps", type=int, default=2)
+    ap.add_argument("--batching", action="store_true",
+                    help="the batching workload (16 metallic systems, one q each) in one batch, against one at a time")
     args = ap.parse_args()
     if args.ppa and (args.real_axis or args.ppa < 0):
         ap.error("--ppa takes a positive count and excludes --real-axis")
@@ -530,7 +627,10 @@ def main():
         import torch.distributed as tdist
         tdist.init_process_group("nccl")
         dist = tdist
-    run_ours(args, rank, world, dist)
+    if args.batching:
+        run_batching(args, rank, world, dist)
+    else:
+        run_ours(args, rank, world, dist)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -13,6 +13,7 @@ from .systems import (  # noqa: F401
     System,
     make_system,
     make_closure_system,
+    make_batching_system,
     make_plane_wave_system,
     truncate_bands,
     cfg_learned,

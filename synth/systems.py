@@ -328,6 +328,53 @@ def truncate_bands(system: System, nb: int) -> System:
                                occ=np.ascontiguousarray(system.occ[:, :nb]))
 
 
+def _smooth_at_least(n: int) -> int:
+    """Smallest 2^a 3^b 5^c >= n (FFT-friendly grid size)."""
+    m = n
+    while True:
+        r = m
+        for f in (2, 3, 5):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return m
+        m += 1
+
+
+def make_batching_system(s: int, nq_max=None, coef_dtype: str = "c64") -> System:
+    """System s of the batching workload (seed 3000 + s): cell edge a ~ U[8, 14]
+    bohr, 4x4x4 k, plane waves per state log-uniform on [400, 4000] (sphere
+    radius from the count), N_G ~ U{200..1500}, N_q ~ U{4..20} distinct nonzero
+    grid vectors, N_w ~ U{8..64} imaginary frequencies on the Gauss-Legendre
+    nodes of [0, 100] eV, 64 bands with energies ~ U[-10, 30] eV sorted per k,
+    Fermi-Dirac occupations at kT = 0.05 eV for 32 electrons per cell (metals:
+    transition counts differ from k to k).  The FFT grid is the smallest
+    2^a 3^b 5^c at least 4 n_max + 1 (n_max the largest Miller index of the
+    spheres) and alias free for the response set.  nq_max keeps only the first
+    nq_max q vectors."""
+    rng = np.random.default_rng(3000 + s)
+    a = float(rng.uniform(8.0, 14.0))
+    npw = float(np.exp(rng.uniform(np.log(400.0), np.log(4000.0))))
+    kc = (3.0 * npw / (4.0 * math.pi)) ** (1.0 / 3.0) * 2.0 * math.pi / a
+    ng = int(rng.integers(200, 1501))
+    nq = int(rng.integers(4, 21))
+    nw = int(rng.integers(8, 65))
+    grid = [(i, j, l) for i in range(4) for j in range(4) for l in range(4) if (i, j, l) != (0, 0, 0)]
+    pick = rng.choice(len(grid), size=nq, replace=False)
+    qs = tuple(tuple(v / 4.0 for v in grid[p]) for p in pick)
+    if nq_max is not None:
+        qs = qs[:nq_max]
+    spec = SystemSpec(a=a, kgrid=(4, 4, 4), n_occ=0, n_bands=64, kc=kc, fft=(8, 8, 8), ng=ng, q_frac=qs,
+                      freqs=tuple(gauss_legendre_freqs(nw, 0.0, 100.0)), eta=0.0, occ_ev=(-10.0, 30.0),
+                      emp_ev=(-10.0, 30.0), kT_ev=0.05, n_electrons=32, seed=3000 + s, coef_dtype=coef_dtype)
+    sysm = make_system(spec)
+    n_max = int(np.abs(sysm.gvec).max())
+    r_g = (3.0 * ng / (4.0 * math.pi)) ** (1.0 / 3.0) + 2.0      # response-set extent, with margin
+    n = _smooth_at_least(max(4 * n_max + 1, 2 * n_max + int(math.ceil(r_g)) + 3))
+    spec = dataclasses.replace(spec, fft=(n, n, n))
+    return dataclasses.replace(sysm, spec=spec, fft=(n, n, n))
+
+
 def cfg_learned(seed: int = 4000, full_bands: int = 800, n_occ: int = 12, kgrid=(6, 6, 6),
                 kc: float = 4.4601, fft=(32, 32, 32), ng: int = 500, nw: int = 16) -> SystemSpec:
     """Learned-terminator case: 6x6x6 k, 12 occupied bands, ~1500 PW, FFT 32^3,
