@@ -5,7 +5,9 @@
 2. for a general input (two poles per element) the model reproduces eps^-1 at
    the two fit frequencies exactly and differs elsewhere;
 3. elements without a real pole (Re wt^2 <= 0, or no frequency dependence)
-   are kept at their static value.
+   are kept at their static value;
+4. the Drude (free-electron) dielectric function: the fit recovers the
+   plasma frequency for any second fit point and reproduces eps^-1 everywhere.
 """
 import numpy as np
 
@@ -62,3 +64,26 @@ def test_elements_without_a_real_pole_stay_static():
     assert wt[1, 0] != 0 and wt[1, 1] != 0
     out = O.ppa_eval(wt, R, [0.0, 2j], 0.0)
     assert out[0][0, 0] == 1.5 and out[1][0, 1] == 0.2
+
+
+
+def test_drude_plasma_frequency_recovered():
+    """The free-electron (Drude) dielectric function eps = 1 - Omega^2 / w^2 has
+    eps^-1(i nu) = nu^2 / (nu^2 + Omega^2): one plasmon at the plasma frequency
+    Omega.  With one Drude element per diagonal entry (and none off the
+    diagonal), the two-point fit must return wt = Omega whatever the second
+    point, keep the off-diagonal zeros static, and reproduce
+    eps^-1 = 1 + Omega^2 / (w^2 - Omega^2) at any frequency."""
+    Omega = np.array([0.35, 0.8, 1.3, 2.6])
+    eye = np.eye(Omega.size)
+    for wp in (0.5, 1.0, 3.0):
+        e0 = np.zeros((Omega.size, Omega.size), complex)                 # eps^-1(0) = 0 on the diagonal
+        ep = np.diag(wp ** 2 / (wp ** 2 + Omega ** 2)).astype(complex)   # eps^-1(i wp)
+        wt, R = O.ppa_fit(e0, ep, wp)
+        assert np.allclose(np.diag(wt), Omega, rtol=1e-12, atol=0)
+        assert np.all(wt[~eye.astype(bool)] == 0) and np.all(R[~eye.astype(bool)] == 0)
+        w = np.array([0.1, 0.9, 4.0, 0.6j]) + 1e-3j
+        model = O.ppa_eval(wt, R, w, 0.0)
+        for k, wk in enumerate(w):
+            want = eye + np.diag(Omega ** 2 / (wk ** 2 - Omega ** 2))
+            assert np.allclose(model[k], want, rtol=1e-10, atol=1e-12)
