@@ -7,7 +7,10 @@ the weights are complex and chi0, eps~ are not Hermitian:
    negative semidefinite (every transition absorbs), and it vanishes as
    eta -> 0 away from the transition energies;
 3. Gauss-Jordan with partial pivoting inverts the general eps~ like LAPACK,
-   and agrees with the RPA route of Eq. (X_rpa_inv).
+   and agrees with the RPA route of Eq. (X_rpa_inv);
+4. causality: the real part of chi0 on the real axis is the Hilbert transform
+   of its imaginary part (Kramers-Kronig, within 1e-4 of the largest value),
+   and the advanced sign of eta fails that by order one.
 """
 import numpy as np
 
@@ -62,3 +65,33 @@ def test_general_inverse_routes():
         assert np.abs(gj @ e - np.eye(len(G))).max() < 1e-12
         assert np.abs(gj - np.linalg.inv(e)).max() < 1e-12 * np.abs(gj).max()
         assert np.abs(gj - O.eps_inv_rpa_route(c, qg)).max() < 1e-12 * np.abs(gj).max()
+
+
+def _pv_integral(x, f, x0):
+    """Principal value of int f(x) / (x - x0) dx over the grid x (trapezoid on the
+    subtracted, smooth integrand plus the closed form of the log term)."""
+    fx0 = np.interp(x0, x, f)
+    g = (f - fx0) / (x - x0)
+    g[np.isclose(x, x0)] = np.gradient(f, x)[np.isclose(x, x0)]
+    return np.trapezoid(g, x) + fx0 * np.log(abs((x[-1] - x0) / (x[0] - x0)))
+
+
+def test_kramers_kronig():
+    """Causality: with +i eta on both poles chi0 is analytic in the upper half
+    plane, so on the real axis its real part is the Hilbert transform of its
+    imaginary part, Re chi(w) = (1/pi) P int Im chi(w') / (w' - w) dw' (here
+    for the head element, w' over the whole real line).  The advanced sign
+    (-i eta) breaks the relation."""
+    s = _sys()
+    G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], 2)
+    eta = 0.2
+    core = np.linspace(-20.0, 20.0, 4001)
+    tail = np.geomspace(20.0, 4000.0, 400)[1:]
+    x = np.concatenate([-tail[::-1], core, tail])
+    for sign, ok in ((1.0, True), (-1.0, False)):
+        chi = O.chi0_tr(s, 0, G, x + 0j, sign * eta)[:, 0, 0]
+        for w0 in (0.3, 0.8, 1.2):
+            re_kk = _pv_integral(x, chi.imag, w0) / np.pi
+            re = np.interp(w0, x, chi.real)
+            err = abs(re_kk - re) / np.abs(chi).max()
+            assert (err < 1e-4) == ok, (sign, w0, err)
