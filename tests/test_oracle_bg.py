@@ -76,3 +76,18 @@ def test_correction_hermitian_on_imaginary_axis():
     d = O.delta_chi_bg(s, 0, G, s.freqs, 0.0, eps_bar=40.0 / HA_EV)
     assert np.abs(d - np.conj(np.transpose(d, (0, 2, 1)))).max() < 1e-13 * np.abs(d).max()
     assert np.abs(d).max() > 0.0
+
+
+def test_closure_exact_on_the_real_axis():
+    """The closure form does not depend on the frequency factor: with every
+    omitted band at eps_bar it reproduces the full-band chi0 at real
+    frequencies with broadening too (complex weights, non-Hermitian chi0)."""
+    eps_bar = 45.0 / HA_EV
+    nb_keep = 12
+    full = make_closure_system(nb_keep=nb_keep, omitted_ev=(eps_bar * HA_EV, eps_bar * HA_EV))
+    G = O.response_gvectors(full.spec.kgrid, full.q_frac[0], full.ng)
+    freqs, eta = np.array([0.2, 0.9, 1.7]) + 0j, 0.05
+    ref = O.chi0_tr(full, 0, G, freqs, eta)
+    got = O.chi0_bg(truncate_bands(full, nb_keep), 0, G, freqs, eta, eps_bar)
+    assert np.abs(ref - np.conj(np.swapaxes(ref, 1, 2))).max() > 1e-3 * np.abs(ref).max()   # not Hermitian
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
