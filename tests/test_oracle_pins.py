@@ -18,6 +18,11 @@ P8  umklapp invariance (another reciprocal-lattice representative of k')
 P9  Dyson: Gauss-Jordan == linear solve of Eq. (X_rpa_inv); eps~^-1
     Hermitian with spectrum in (0, 1]; Gauss-Jordan == LAPACK inverse
 P10 high-frequency tail: w^2 chi0(iw) -> -f_s/(N_k Omega) sum_t 2|D_t| df rho rho^H
+P13 absolute scale: the f-sum (Thomas-Reiche-Kuhn) rule of a free-electron
+    crystal, nu^2 chi0_GG(i nu) -> -(N_el/Omega) |q+G|^2, with N_el counted
+    from the occupations and Omega = a^3, so the prefactor f_s/(N_k Omega)
+    and the 2 pi/a of the reciprocal lattice are fixed by physics, not by the
+    oracle's own formula; |q+G| checked against values worked out by hand
 G-set: the response G order for q = (1/4,0,0) written out by hand.
 """
 import math
@@ -281,3 +286,95 @@ def test_p9_dyson_routes(tiny3):
         ev = np.linalg.eigvalsh(0.5 * (e1 + e1.conj().T))
         assert ev.min() > 0 and ev.max() <= 1 + 1e-12 and ev.min() < 0.999
         assert np.abs(e1 @ O.eps_tilde(c, qg) - np.eye(len(G))).max() < 1e-12
+
+
+# ---------------------------------------------------------------- absolute scale (P13)
+
+
+def _fsum_system():
+    """Free-electron crystal with few occupied plane waves and enough bands
+    that every occupied momentum p has p + (q+G) and p - (q+G) in the band
+    sets, for every G of the response set (checked below from momenta)."""
+    spec = cfg_tiny(kgrid=(2, 2, 2), n_bands=40, npw_target=None, kc=3.0,
+                    q_frac=((0.5, 0.0, 0.0),), eta=0.0)
+    s = make_plane_wave_system(spec, e_fermi=0.15)
+    G = O.response_gvectors(spec.kgrid, s.q_frac[0], 7)
+    return s, G
+
+
+def _band_momenta(s, ik):
+    """Momentum k + G of every band (in units of 2 pi / a), doubled to integers
+    (the k grid is 2x2x2 and q = (1/2, 0, 0))."""
+    g = s.sphere(ik)[np.argmax(np.abs(s.coefs(ik)), axis=1)]
+    return np.rint(2.0 * (s.kfrac[ik][None, :] + g)).astype(np.int64)
+
+
+def _fsum_deviation(s, G, chi_fn):
+    """max |nu^2 chi0_GG(i nu) + (N_el/Omega)|q+G|^2| / max |(N_el/Omega)|q+G|^2|
+    and the largest off-diagonal |nu^2 chi0|, at nu = 1e5 Ha."""
+    nu = 1.0e5
+    chi = chi_fn(s, 0, G, [1j * nu], 0.0)[0] * nu * nu
+    n_el = s.spin_factor * float(s.occ.sum()) / s.nk      # electrons per cell
+    volume = s.spec.a ** 3                                # cubic cell (bohr^3)
+    two_pi_a = 2.0 * math.pi / s.spec.a                   # reciprocal lattice step
+    qg2 = (two_pi_a ** 2) * ((s.q_frac[0][None, :] + G) ** 2).sum(axis=1)
+    expect = -(n_el / volume) * qg2
+    dev = np.abs(np.diag(chi) - expect).max() / np.abs(expect).max()
+    off = np.abs(chi - np.diag(np.diag(chi))).max() / np.abs(expect).max()
+    return dev, off
+
+
+def test_p13_fsum_preconditions():
+    s, G = _fsum_system()
+    held = set()
+    for ik in range(s.nk):
+        held |= {tuple(p) for p in _band_momenta(s, ik).tolist()}
+    q2 = np.rint(2.0 * s.q_frac[0]).astype(np.int64)
+    n_occ = 0
+    for ik in range(s.nk):
+        mom = _band_momenta(s, ik)
+        for b in np.nonzero(s.occ[ik] > 0)[0]:
+            n_occ += 1
+            for Gv in G:
+                Q = q2 + 2 * Gv
+                assert tuple((mom[b] + Q).tolist()) in held
+                assert tuple((mom[b] - Q).tolist()) in held
+    assert 1 < n_occ < s.occ.size
+
+
+@pytest.mark.parametrize("form", ["tr", "all_pairs"])
+def test_p13_fsum_rule(form):
+    s, G = _fsum_system()
+    fn = O.chi0_tr if form == "tr" else O.chi0_all_pairs
+    dev, off = _fsum_deviation(s, G, fn)
+    assert dev < 1e-9 and off < 1e-12
+
+
+def test_p13_fsum_teeth(monkeypatch):
+    """The f-sum check fails on the plausible prefactor mistakes, planted in
+    the oracle: the spin factor dropped, or Omega in place of N_k Omega."""
+    import oracle.chi0 as oc
+    s, G = _fsum_system()
+    for wrong in (lambda sy: 1.0 / (sy.nk * sy.omega_cell),
+                  lambda sy: sy.spin_factor / sy.omega_cell):
+        monkeypatch.setattr(oc, "_prefactor", wrong)
+        dev, _ = _fsum_deviation(s, G, O.chi0_tr)
+        assert dev > 0.4
+
+
+def _qg_literal_ok(qg_fn):
+    """|q+G| in bohr^-1 for a = 10 bohr and q = (1/4, 0, 0), worked out by hand:
+    G = 0: 2 pi/10 * 1/4 = 0.05 pi; G = (1,0,0): 2 pi/10 * 5/4 = 0.25 pi;
+    G = (-1,0,0): 0.15 pi; G = (0,1,0): 0.2 pi * sqrt(17)/4; G = (1,1,1):
+    0.2 pi * sqrt(57)/4."""
+    G = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [1, 1, 1]])
+    expect = math.pi * np.array([0.05, 0.25, 0.15, 0.05 * math.sqrt(17.0), 0.05 * math.sqrt(57.0)])
+    got = qg_fn(10.0, np.array([0.25, 0.0, 0.0]), G)
+    return np.abs(got - expect).max() < 1e-15
+
+
+def test_p13_qg_norm_literal():
+    assert _qg_literal_ok(O.qg_norms)
+    # teeth: the reciprocal-lattice factor 2 pi/a dropped, or 1/a kept alone
+    assert not _qg_literal_ok(lambda a, q, g: np.sqrt(((q[None, :] + g) ** 2).sum(axis=1)))
+    assert not _qg_literal_ok(lambda a, q, g: np.sqrt(((q[None, :] + g) ** 2).sum(axis=1)) / a)
