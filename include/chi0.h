@@ -227,8 +227,9 @@ chi0_status chi0_get_stats(chi0_ctx* ctx, double* ms, double* bytes, double* flo
 
 /* Allocation-free eps~^-1 for callers that cannot allocate device memory.
  * The paper has no counterpart: this exists for code whose device memory is
- * owned by another allocator, that must keep a fixed device footprint once
- * running, or that is inside a stream capture, where cudaMalloc is not allowed.
+ * owned by another allocator (which must account for every byte), or that
+ * must keep a fixed device footprint once running (so that no later
+ * allocation can fail or take memory from another tenant of the GPU).
  * It computes the same result as chi0_invert_eps from a chi0 the caller holds:
  *   chi0:   device pointer, [nw][ng][ng] complex128 (input, not modified);
  *   v_sqrt: host pointer, [ng] doubles, V_i = sqrt(4 pi) / |q + G_i| (> 0);

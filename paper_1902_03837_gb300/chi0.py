@@ -132,13 +132,24 @@ def _ptr(a):
 def invert_eps_noalloc(chi0, v_sqrt, out, stream=None):
     """chi0_invert_eps_noalloc: eps~^-1 without device allocation.
     chi0, out: contiguous complex128 CUDA tensors [nw][ng][ng]; v_sqrt: host
-    float64 [ng].  Raises Chi0Error on a non-zero status."""
+    float64 [ng].  Raises ValueError on mismatched arguments and Chi0Error on
+    a non-zero status."""
+    import torch
+    for name, t in (("chi0", chi0), ("out", out)):
+        if getattr(t, "dtype", None) != torch.complex128:
+            raise ValueError(f"{name} must be a complex128 tensor")
+        if t.dim() != 3 or t.shape[1] != t.shape[2] or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous [nw][ng][ng] tensor")
+    if tuple(out.shape) != tuple(chi0.shape):
+        raise ValueError("out must have the shape of chi0")
+    v = np.ascontiguousarray(v_sqrt, dtype=np.float64).reshape(-1)
+    nw, ng = int(chi0.shape[0]), int(chi0.shape[1])
+    if v.size != ng:
+        raise ValueError(f"v_sqrt has {v.size} entries, expected ng = {ng}")
     cp, cdev = _ptr(chi0)
     op, odev = _ptr(out)
     if not (cdev and odev):
         raise ValueError("chi0 and out must be device tensors")
-    v = np.ascontiguousarray(v_sqrt, dtype=np.float64)
-    nw, ng = int(chi0.shape[0]), int(chi0.shape[1])
     st = _lib.chi0_invert_eps_noalloc(cp, v.ctypes.data, ng, nw, op, stream)
     if st != 0:
         raise Chi0Error(st, "chi0_invert_eps_noalloc failed")

@@ -1,15 +1,18 @@
 // chi0_invert_eps_noalloc: the Dyson inversion without any device allocation.
 //
 // Some callers cannot call cudaMalloc: code whose device memory is owned by
-// another allocator (a framework's caching allocator that must see every
-// byte), processes that must keep a fixed device-memory footprint once they
-// have started, or callers in the middle of a stream capture, where an
-// allocation is not allowed.  This entry point runs the same blocked
-// Gauss-Jordan kernels as chi0_invert_eps, one frequency after another, with
-// all of their scratch (the row/column panels, the pivot-block inverse, the
-// Coulomb factors and the error flag) in one file-scope device array whose
-// size is fixed at build time.  Every GPU that loads the library holds that
-// array until the process exits.
+// another allocator (a framework's caching allocator that must account for
+// every byte it hands out), or a service that must keep a fixed device-memory
+// footprint once it has started, so that a later allocation can neither fail
+// nor push another tenant of the GPU out of memory.  This entry point runs the
+// same blocked Gauss-Jordan kernels as chi0_invert_eps, one frequency after
+// another, with all of their scratch (the row/column panels, the pivot-block
+// inverse, the Coulomb factors and the error flag) in one file-scope device
+// array whose size is fixed at build time.  Every GPU that loads the library
+// holds that array until the process exits.  The first call on a device
+// looks up the array's device address (cudaGetSymbolAddress, once per
+// device, with that device current); make that first call before any stream
+// capture begins.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -135,6 +135,27 @@ def test_new_entry_points_reject_bad_arguments(binding):
     c.close()
 
 
+def test_noalloc_wrapper_rejects_mismatched_arguments(binding):
+    """invert_eps_noalloc checks dtype, shape, contiguity and the length of
+    v_sqrt before it calls the library (a short v_sqrt would be read past its
+    end, a smaller out written past its end)."""
+    import torch
+    ok = torch.zeros((2, 5, 5), dtype=torch.complex128)
+    v = np.ones(5)
+    cases = [
+        (ok.to(torch.complex64), v, ok),                 # wrong dtype of chi0
+        (ok, v, ok.to(torch.complex64)),                 # wrong dtype of out
+        (torch.zeros((2, 5, 4), dtype=torch.complex128), v, ok),   # not square
+        (ok, v, torch.zeros((1, 5, 5), dtype=torch.complex128)),   # shapes differ
+        (ok.transpose(1, 2), v, ok),                     # not contiguous
+        (ok, np.ones(4), ok),                            # short v_sqrt
+        (ok, v, ok),                                     # host tensors
+    ]
+    for c, vv, o in cases:
+        with pytest.raises(ValueError):
+            binding.invert_eps_noalloc(c, vv, o)
+
+
 def test_injected_allocation_failure(binding, monkeypatch):
     c = _ctx(binding)
     monkeypatch.setenv("CHI0_FAULT", "alloc")

@@ -1,8 +1,9 @@
 """The allocation-free Dyson entry point (chi0_invert_eps_noalloc).
 
 Callers that cannot allocate device memory (memory owned by another
-allocator, a fixed device footprint, or work inside a stream capture) use
-this entry point; its scratch is a static device array.  Two calls in a row
+allocator that must account for every byte, or a service held to a fixed
+device footprint) use this entry point; its scratch is a static device
+array.  Two calls in a row
 must agree with chi0_invert_eps, the allocating entry point, within the FP64
 tolerance of the other GPU tests (1e-10 relative), which also shows that the
 second call starts from a clean error flag and overwrites the first call's
