@@ -68,14 +68,44 @@ STAGE_ROOF = {"contract": ("tensor", "TFLOP/s", "k_herk_bf16x3"), "rho": ("alu",
 FP32_PEAK, FP32_SRC = 75.0, "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 1.93 GHz"
 # FP64: the nominal GB300 figure (no measured FP64 peak is available)
 FP64_PEAK, FP64_SRC = 1.25, "FP64 nominal (GB300)"
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel on
-# this workload (one-pass dram__bytes_read.sum + dram__bytes_write.sum at full
-# size); to be removed once the kernel changes after the capture.
-TRAFFIC = {
-    ("k_herk_bf16x3", WORKLOAD): (5.37e10, "ncu, mean of 6 full-size launches (one frequency each)"),
-    ("k_rho_pairs", WORKLOAD): (4.42e10, "ncu, one full-size launch"),
-    ("k_prep", WORKLOAD): (1.17e11, "ncu, one full-size eight-frequency pass"),
-}
+# Stored DRAM traffic per launch (ncu, dram__bytes_read.sum +
+# dram__bytes_write.sum) is read from the profile summaries under profiles/:
+# lines of the form
+#   traffic: <kernel> | <workload> | <bytes per launch> | <source file> <sha256 prefix> | <how>
+# A figure is used only while the kernel's source file still has the hash it
+# had when the counters were taken; after any change it reads as null.
+KERNEL_SOURCE = {"k_herk_bf16x3": "tc.cu", "k_prep": "tc.cu", "k_rho_pairs": "rho.cu",
+                 "k_wf_to_mixed": "rho.cu", "k_gj_update": "dyson.cu", "k_chi0_fp64": "chi0_fp64.cu"}
+
+
+def source_sha(fname):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1902_03837_gb300", "csrc", fname)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def stored_traffic(kernel, workload):
+    """(bytes per launch, description) of the stored ncu figure for kernel on
+    workload, or (None, reason)."""
+    import glob
+    src = KERNEL_SOURCE.get(kernel)
+    found = None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                if not line.startswith("traffic:"):
+                    continue
+                parts = [x.strip() for x in line[len("traffic:"):].split("|")]
+                if len(parts) < 5 or parts[0] != kernel or parts[1] != workload:
+                    continue
+                found = (float(parts[2]), parts[3].split(), parts[4], os.path.basename(path))
+    if found is None or src is None:
+        return None, "no stored ncu figure for this kernel and workload"
+    nbytes, (fname, sha), how, where = found
+    if fname != src or sha != source_sha(src):
+        return None, f"the kernel's source changed since the stored ncu figure ({where})"
+    return nbytes, f"{how} ({where}, {fname} {sha})"
 
 
 def peaks():
@@ -177,11 +207,164 @@ def workload_name(args):
     return base
 
 
+def workload_tag(args):
+    """Short name of the workload for the stored ncu figures."""
+    k = "x".join(str(v) for v in (args.kgrid or (8, 8, 8)))
+    tag = f"precision k{k} nw{args.nw}"
+    if getattr(args, "real_axis", False):
+        tag += " real"
+    if getattr(args, "ppa", None):
+        tag += f" ppa{args.ppa}"
+    if getattr(args, "bg_terminator", None) is not None:
+        tag += " bg"
+    if getattr(args, "precision", "mixed") == "fp64":
+        tag += " fp64"
+    return tag
+
+
+def stage_rooflines(args, st_ms, st_bytes, st_flops, pk, nt, ng, nw):
+    """Achieved rate of every stage against the roof that binds it, per step:
+    rho and the wavefunction transforms against the FP32 (or FP64) pipe and
+    HBM, the operand split against HBM, the contraction against the tensor
+    cores (algorithmic count), the Dyson step against the FP64 units."""
+    out = {}
+    fp64 = args.precision == "fp64"
+    for st in ("wf_grid", "rho", "weights", "contract", "reduce", "dyson"):
+        ms = st_ms[st] / args.steps
+        if ms <= 0:
+            continue
+        sec = ms * 1e-3
+        gbs = st_bytes[st] / sec / 1e9
+        tfs = st_flops[st] / sec / 1e12
+        e = {"ms_per_step": ms, "gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "tflops": tfs}
+        if st in ("wf_grid", "rho"):
+            peak, src = (FP64_PEAK, FP64_SRC) if fp64 else (FP32_PEAK, FP32_SRC)
+            e.update(bound="fp64" if fp64 else "alu", alu_peak=peak, alu_frac=tfs / peak, alu_peak_source=src)
+        elif st == "contract":
+            if fp64:
+                e.update(bound="fp64", alu_peak=FP64_PEAK, alu_frac=tfs / FP64_PEAK, alu_peak_source=FP64_SRC)
+            else:
+                e.update(bound="tensor", tensor_peak=pk["bf16_tflops_sustained"],
+                         tensor_frac=tfs / pk["bf16_tflops_sustained"])
+        elif st == "dyson":
+            e.update(bound="fp64", alu_peak=FP64_PEAK, alu_frac=tfs / FP64_PEAK, alu_peak_source=FP64_SRC)
+        else:
+            e.update(bound="hbm")
+        out[st] = e
+    return out
+
+
 def _workload_base(args):
     if args.kgrid is None and args.nw == 32:
         return WORKLOAD
     k = "x".join(str(v) for v in (args.kgrid or (8, 8, 8)))
     return WORKLOAD.replace("k 8x8x8", f"k {k}").replace("32 imaginary", f"{args.nw} imaginary")
+
+
+# ----------------------------------------------------------------------------- CPU baseline (the oracle)
+
+# The CPU baseline leg: the oracle's chi0 on the G_0..G_63 sub-block of the
+# benchmark's own system (all transitions, all frequencies), summed over k
+# chunks by worker processes, and the oracle's Gauss-Jordan inversion of two
+# of the GPU's eps~.  Its time is the reported CPU baseline; its results give
+# the error of the GPU path.  The workers are spawned (no GPU state), read the
+# system from files the parent writes, and run on every host core but the
+# first, which keeps issuing the GPU work.
+ERR_G = 64                  # G_0 .. G_63: the real tile (0, 0) of the contraction
+_ERR = {}
+_SYS_ARRAYS = ("lattice", "kfrac", "npw", "gvec", "coef", "eps", "occ", "q_frac", "freqs")
+
+
+def _err_init(path, cores):
+    """Worker set-up: one thread each, pinned to the worker cores; the
+    system's arrays mapped read-only from the files the parent wrote."""
+    import pickle
+    try:
+        os.sched_setaffinity(0, cores)
+    except (AttributeError, OSError):
+        pass
+    with open(os.path.join(path, "system.pkl"), "rb") as f:
+        meta = pickle.load(f)
+    arrays = {k: np.load(os.path.join(path, k + ".npy"), mmap_mode="r") for k in _SYS_ARRAYS}
+    from synth import System
+    _ERR["s"] = System(**meta["fields"], **arrays)
+    _ERR["G"] = meta["G"]
+
+
+def _err_chunk(ks):
+    import oracle as O
+    s = _ERR["s"]
+    return O.chi0_tr(s, 0, _ERR["G"], s.freqs, s.eta, ks=ks)
+
+
+def _err_gj(chi, qg):
+    import oracle as O
+    return O.eps_inv_gauss_jordan(chi, qg)
+
+
+class OracleJobs:
+    """Worker processes (spawned, one thread each, on every host core but the
+    first) that run the oracle for the CPU baseline leg."""
+
+    def __init__(self, system):
+        import multiprocessing as mp
+        import pickle
+        import tempfile
+        import oracle as O
+        G = O.response_gvectors(system.spec.kgrid, system.q_frac[0], system.ng)
+        self.qg = O.qg_norms(system.spec.a, system.q_frac[0], G)
+        self.tmp = tempfile.TemporaryDirectory(prefix="chi0_baseline_")
+        for k in _SYS_ARRAYS:
+            np.save(os.path.join(self.tmp.name, k + ".npy"), np.ascontiguousarray(getattr(system, k)))
+        fields = {k: getattr(system, k) for k in ("spec", "omega_cell", "eta", "spin_factor", "fft", "ng")}
+        with open(os.path.join(self.tmp.name, "system.pkl"), "wb") as f:
+            pickle.dump({"fields": fields, "G": G[:ERR_G]}, f)
+        try:
+            cores = sorted(os.sched_getaffinity(0))
+        except AttributeError:
+            cores = list(range(os.cpu_count() or 1))
+        work = set(cores[1:]) or set(cores)
+        self.nproc = len(work)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.nproc, initializer=_err_init,
+                                                     initargs=(self.tmp.name, work))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.nk = system.nk
+        self.chunks = None
+        self.gj = []
+
+    def start_chi0(self):
+        ks = list(range(self.nk))
+        step = max(1, -(-self.nk // (4 * self.nproc)))
+        self.t0 = time.perf_counter()
+        self.chunks = self.pool.map_async(_err_chunk, [ks[i:i + step] for i in range(0, self.nk, step)])
+
+    def start_gj(self, chi):
+        self.gj.append(self.pool.apply_async(_err_gj, (chi, self.qg)))
+
+    def chi0(self):
+        parts = self.chunks.get()
+        return sum(parts[1:], parts[0]), time.perf_counter() - self.t0
+
+    def gj_results(self):
+        return [r.get() for r in self.gj]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.tmp.cleanup()
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -236,6 +419,15 @@ def run_reference(args, rank, world):
 
 def run_ours(args, rank, world, dist):
     import torch
+    s = build_system(args.kgrid, args.nw, args.real_axis, ppa=bool(args.ppa))
+    ng, nw = s.ng, s.freqs.size
+    # the plain FP64 form and the CPU baseline on the G_0..G_63 sub-block (with
+    # the error against it) are measured on the imaginary-axis workload (rank
+    # 0 only); the baseline's workers start here, before any CUDA call
+    plain = (rank == 0 and args.precision == "mixed" and not args.ppa and not args.real_axis
+             and args.bg_terminator is None)
+    compare = plain and not args.no_compare
+    jobs = OracleJobs(s) if (plain and not args.no_cpu_baseline) else None
     import __graft_entry__ as g
     g.build()
     from paper_1902_03837_gb300 import chi0 as lib
@@ -244,8 +436,6 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    s = build_system(args.kgrid, args.nw, args.real_axis, ppa=bool(args.ppa))
-    ng, nw = s.ng, s.freqs.size
     prec = lib.CHI0_MIXED_BF16X3 if args.precision == "mixed" else lib.CHI0_FP64
     ctx = lib.Chi0.for_system(s, precision=prec, stream=stream.cuda_stream)
     # inputs resident in HBM (device-to-device set keeps the timed region free of host copies)
@@ -332,23 +522,37 @@ def run_ours(args, rank, world, dist):
     h2d = sum(int(x.numel() * x.element_size()) for x in pin_gv + pin_cf) + 2 * s.eps.nbytes
     d2h = int(out_h.numel() * out_h.element_size())
 
+    # host wall time of each call of an end-to-end step (the calls return as
+    # soon as their work is queued, except the last, which copies the result
+    # to the host and waits for it)
+    phase_ms = {"set_wavefunctions": 0.0, "set_energies": 0.0, "compute_rho": 0.0, "build_invert_and_copy": 0.0}
+
     def e2e_step():
+        t = [time.perf_counter()]
         for ik in range(s.nk):
             ctx.set_wavefunctions(ik, pin_gv[ik], pin_cf[ik])
+        t.append(time.perf_counter())
         ctx.set_energies(s.eps, s.occ)
+        t.append(time.perf_counter())
         ctx.compute_rho(0)
+        t.append(time.perf_counter())
         if args.ppa:
             ctx.build_invert(0, inv_d)
             ppa_step(False)
             out_h.copy_(model_d)     # the model on the real axis, device -> host
         else:
             ctx.build_invert(0, out_h)   # device -> host copy of the result, synchronises
+        t.append(time.perf_counter())
+        for k, a, b in zip(phase_ms, t[:-1], t[1:]):
+            phase_ms[k] += (b - a) * 1e3
 
     e2e_clk = None
     if args.no_e2e:
         e2e_ms = None
     else:
         e2e_step()
+        for k in phase_ms:
+            phase_ms[k] = 0.0
         e2e_steps = max(1, min(args.steps, 3))
         barrier()
         torch.cuda.synchronize(dev)
@@ -360,6 +564,21 @@ def run_ours(args, rank, world, dist):
             barrier()
             e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
         e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+        phase_ms = {k: v / e2e_steps for k, v in phase_ms.items()}
+    # data for the error against the oracle: one more step with chi0 kept
+    cmp_data = None
+    if jobs is not None:
+        jobs.start_chi0()
+        chi_d = torch.empty_like(inv_d)
+        ctx.compute_rho(0)
+        ctx.build_invert(0, inv_d, chi_d)
+        torch.cuda.synchronize(dev)
+        two = [0, nw - 1]
+        cmp_data = {"chi_sub": chi_d[:, :ERR_G, :ERR_G].cpu().numpy(),
+                    "chi_two": chi_d[two].cpu().numpy(), "inv_two": inv_d[two].cpu().numpy(), "two": two}
+        for m in cmp_data["chi_two"]:
+            jobs.start_gj(m)
+        del chi_d
     sigma_line = None
     if args.sigma:
         # the self-energy kernel I (Eq. I_c) on the real-axis eps~^-1 of this
@@ -393,6 +612,10 @@ def run_ours(args, rank, world, dist):
                       "dot_y_gbs": ybytes / (sms["reduce"] * 1e-3) / 1e9}
     ctx.get_stats()
     ctx.close()
+    fp64_line = fp64_form(args, lib, s, nt, stream, dev) if compare else None
+    base_line = None
+    if jobs is not None:
+        base_line = baseline_and_error(s, nt, jobs, cmp_data, fp64_line)
 
     if rank != 0:
         return
@@ -431,12 +654,11 @@ def run_ours(args, rank, world, dist):
     else:
         achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
         peak, psrc = FP32_PEAK, FP32_SRC
-    traffic, tsrc = TRAFFIC.get((kname, workload_name(args)), (None, None)) if args.precision == "mixed" else (None, None)
+    traffic, tsrc = stored_traffic(kname, workload_tag(args))
     roof = {"kernel": kname, "stage": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "peak_source": psrc, "traffic": traffic}
-    if tsrc:
-        roof["traffic_source"] = tsrc
+            "frac": achieved / peak, "peak_source": psrc, "traffic": traffic, "traffic_source": tsrc}
     roof.update(extra)
+    stages = stage_rooflines(args, st_ms, st_bytes, st_flops, pk, nt, ng, nw)
     ppa_line = None
     if args.ppa:
         n2 = ng * ng
@@ -461,9 +683,11 @@ def run_ours(args, rank, world, dist):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "stage_ms_per_step": per_step_ms,
         "roofline": roof,
+        "stage_roofline": stages,
         "e2e": (None if e2e_ms is None else
                 {"value": whole_job_tflops(world, flops_step, e2e_ms), "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "phase_host_ms_per_step": phase_ms,
                  # the e2e steps follow the timed region: the SM clock they ran at
                  "clocks": e2e_clk.summary() if e2e_clk is not None else None}),
         "gpu_launches": int(launches),
@@ -477,7 +701,16 @@ def run_ours(args, rank, world, dist):
         sg["contract_peak_source"] = f"BF16 dense sustained ({pk['source']})"
         sg["dot_y_hbm_frac"] = sg["dot_y_gbs"] / pk["hbm_gbs"]
         line["sigma"] = sg
-    if not args.no_cpu_baseline:
+    if fp64_line is not None:
+        f = {k: v for k, v in fp64_line.items() if not k.startswith("_")}
+        f["speedup_vs_fp64_form_measured"] = f["ms_per_step"] / f["mixed_ms_per_step"]
+        f["speedup_vs_fp64_form_derived_at_nw"] = f["derived_ms_at_nw"] / ms_step
+        line["fp64_form"] = f
+    if base_line is not None:
+        line["cpu_baseline"], line["error"] = base_line
+    elif fp64_line is not None:
+        line["error"] = {"eps_inv_mixed_vs_fp64_form": fp64_line["_eps_vs_fp64"]}
+    if not args.no_cpu_baseline and base_line is None:
         import oracle as O
         G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
         nks = 4
@@ -489,11 +722,103 @@ def run_ours(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def fp64_form(args, lib, s, nt, stream, dev):
+    """The plain FP64 form of the same step on the first FP64_NW frequencies
+    (one step, timed by CUDA events on the stream its kernels run on), and the
+    mixed form on the same frequencies for the equal-work ratio.  The derived
+    FP64 time for all frequencies is the measured one with its
+    frequency-dependent stages scaled linearly (stated as derived)."""
+    import dataclasses
+    import torch
+    nwf = min(args.fp64_nw, s.freqs.size)
+    s2 = dataclasses.replace(s, freqs=s.freqs[:nwf])
+    ng = s.ng
+
+    def run(prec, steps, warm):
+        ctx = lib.Chi0.for_system(s2, precision=prec, stream=stream.cuda_stream)
+        gv = [torch.from_numpy(np.ascontiguousarray(s2.gvec[ik, :s2.npw[ik]])).to(dev) for ik in range(s2.nk)]
+        cf = [torch.from_numpy(np.ascontiguousarray(s2.coef[ik, :, :s2.npw[ik]])).to(dev) for ik in range(s2.nk)]
+        for ik in range(s2.nk):
+            ctx.set_wavefunctions(ik, gv[ik], cf[ik])
+        ctx.set_energies(s2.eps, s2.occ)
+        del gv, cf
+        inv = torch.empty((nwf, ng, ng), dtype=torch.complex128, device=dev)
+        chi = torch.empty_like(inv)
+        for _ in range(warm):
+            ctx.compute_rho(0)
+            ctx.build_invert(0, inv, chi)
+        ctx.synchronize()
+        ctx.get_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.compute_rho(0)
+            ctx.build_invert(0, inv, chi)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        sms, _, _, _ = ctx.get_stats()
+        out = (ms, {k: v / steps for k, v in sms.items()}, chi[:, :ERR_G, :ERR_G].cpu().numpy(), inv.cpu().numpy())
+        ctx.close()
+        del inv, chi
+        torch.cuda.empty_cache()
+        return out
+
+    mixed_ms, _, _, inv_mixed = run(lib.CHI0_MIXED_BF16X3, 2, 1)
+    with ClockSampler(int(dev.index or 0)) as clk:
+        f_ms, f_stage, f_chi_sub, inv_f = run(lib.CHI0_FP64, 1, 0)
+    freq_ms = f_stage["weights"] + f_stage["contract"] + f_stage["reduce"] + f_stage["dyson"]
+    derived = f_ms + freq_ms * (s.freqs.size / nwf - 1.0)
+    return {"frequencies": nwf, "ms_per_step": f_ms, "stage_ms_per_step": f_stage,
+            "mixed_ms_per_step": mixed_ms, "ms_per_frequency": freq_ms / nwf,
+            "derived_ms_at_nw": derived,
+            "derived_note": f"measured at {nwf} frequencies; the frequency-dependent stages scaled to "
+                            f"{s.freqs.size} (derived, not measured)",
+            "tflops": chi0_flops(ng, nt, nwf) / (f_ms * 1e-3) / 1e12,
+            "mixed_tflops": chi0_flops(ng, nt, nwf) / (mixed_ms * 1e-3) / 1e12, "clocks": clk.summary(),
+            "_chi_sub": f_chi_sub,
+            "_eps_vs_fp64": {"frequencies": list(range(nwf)),
+                             "values": [rel_fro(inv_mixed[i], inv_f[i]) for i in range(nwf)],
+                             "note": "mixed-form eps~^-1 against the plain FP64 form's (full N_G)"}}
+
+
+def baseline_and_error(s, nt, jobs, cmp_data, fp64_line):
+    """The CPU baseline leg's results: its time (the baseline) and the errors
+    of the GPU path against it."""
+    ref, t_oracle = jobs.chi0()
+    gj = jobs.gj_results()
+    jobs.close()
+    nw = s.freqs.size
+    per_w = [rel_fro(cmp_data["chi_sub"][i], ref[i]) for i in range(nw)]
+    err = {
+        "what": "relative Frobenius error ||X - X_oracle||_F / ||X_oracle||_F per frequency",
+        "chi0_subblock": {"g_indices": f"0..{ERR_G - 1}", "max": max(per_w), "median": float(np.median(per_w)),
+                          "per_frequency": per_w, "tolerance": 1e-5},
+        "eps_inv_dyson_vs_oracle_gauss_jordan": {
+            "frequencies": cmp_data["two"],
+            "values": [rel_fro(cmp_data["inv_two"][j], gj[j]) for j in range(len(gj))],
+            "note": "the GPU's eps~^-1 at full N_G against the oracle's Gauss-Jordan inversion of eps~ "
+                    "built from the GPU's own chi0 (isolates the Dyson step)"},
+    }
+    if fp64_line is not None:
+        nwf = fp64_line["frequencies"]
+        err["chi0_subblock_fp64_form"] = [rel_fro(fp64_line["_chi_sub"][i], ref[i]) for i in range(nwf)]
+        err["eps_inv_mixed_vs_fp64_form"] = fp64_line["_eps_vs_fp64"]
+    flops = chi0_flops(ERR_G, nt, nw)
+    base = {"value": flops / t_oracle / 1e12, "unit": "TFLOP/s", "cores": jobs.nproc, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, the G_0..G_{ERR_G - 1} sub-block of chi0 over all {nt} transitions and "
+                      f"{nw} frequencies (rho by direct convolution for those G), k points split over "
+                      f"{jobs.nproc} worker processes; TFLOP/s of the 4 N_G (N_G + 1) N_T N_w count at N_G = {ERR_G}",
+            "seconds": t_oracle}
+    return base, err
+
+
 def run_batching(args, rank, world, dist):
-    """The batching workload: 16 seeded metallic systems of different sizes
-    (one q point each), all problems in one batch (one persistent rho launch,
-    every other kernel in one CUDA graph), against the same problems one at a
-    time, and the first system in the plain FP64 form."""
+    """The batching workload: 16 seeded metallic systems of different sizes,
+    every q point of each (4-20 per system, 200 problems), all in one batch
+    (one persistent rho launch, every other kernel in one CUDA graph; the q
+    points of a system share its mixed grids), against the same problems one
+    at a time, and the first problem in the plain FP64 form."""
     import torch
     import __graft_entry__ as g
     g.build()
@@ -504,49 +829,67 @@ def run_batching(args, rank, world, dist):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     st = stream.cuda_stream
-    systems = [make_batching_system(s_, nq_max=1) for s_ in range(16)]
-    ctxs, outs = [], []
+    systems = [make_batching_system(s_, nq_max=args.batch_nq) for s_ in range(args.batch_systems)]
+    probs = [(si, iq) for si, sy in enumerate(systems) for iq in range(sy.q_frac.shape[0])]
+    outs = [torch.empty((systems[si].freqs.size, systems[si].ng, systems[si].ng), dtype=torch.complex128,
+                        device=dev) for si, _ in probs]
+    ctxs = []
     for sy in systems:
         c = lib.Chi0.for_system(sy, precision=lib.CHI0_MIXED_BF16X3, stream=st, occ_drop_tol=1e-12)
         c.load_system(sy)
         ctxs.append(c)
-        outs.append(torch.empty((sy.freqs.size, sy.ng, sy.ng), dtype=torch.complex128, device=dev))
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(ctxs) + 2)]
-
-    def one_at_a_time():
-        for i, c in enumerate(ctxs):
-            ev[2 * i].record(stream)
-            c.compute_rho(0)
-            c.build_invert(0, outs[i])
-            ev[2 * i + 1].record(stream)
-        torch.cuda.synchronize(dev)
-        return [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ctxs))]
-
-    one_at_a_time()                                  # plans every problem
-    nts = [c.get_transitions().shape[0] for c in ctxs]
-    flops = sum(chi0_flops(sy.ng, nt, sy.freqs.size) for sy, nt in zip(systems, nts))
-    seq = [one_at_a_time() for _ in range(2)]
-    seq_ms = min(sum(r) for r in seq)
-    per_problem = [min(r[i] for r in seq) for i in range(len(ctxs))]
-    batch = lib.Batch(ctxs, [0] * len(ctxs), outs, nstreams=4)
+    t0 = time.perf_counter()
+    batch = lib.Batch([ctxs[si] for si, _ in probs], [iq for _, iq in probs], outs, nstreams=args.batch_streams)
+    create_s = time.perf_counter() - t0
+    streams_of, tuned_ms = batch.info()
+    width = batch.rho_width()
     for _ in range(args.warmup):
         batch.run(st)
-    torch.cuda.synchronize(dev)
-    e0, e1 = ev[-2], ev[-1]
+    batch.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     with ClockSampler(local) as clk:
-        e0.record(stream)
+        ev[0].record(stream)
         for _ in range(args.steps):
             batch.run(st)
-        e1.record(stream)
+        ev[1].record(stream)
         torch.cuda.synchronize(dev)
-    for c in ctxs:
-        c.synchronize()
-    batch_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
-    width = batch.rho_width()
+    batch.synchronize()
+    batch_ms = max_over_ranks(ev[0].elapsed_time(ev[1]) / args.steps, dist, dev)
+    keep = outs[0].clone()
     batch.close()
     for c in ctxs:
         c.close()
-    # the plain FP64 form of the first system, for the speedup at the same size
+    torch.cuda.empty_cache()
+    # the same problems one at a time, each system in a context of its own
+    # (device time of compute_rho + build_invert per problem, after one
+    # untimed pass over the system's q points)
+    per_problem = [0.0] * len(probs)
+    nts = [0] * len(probs)
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(2 * len(probs))]
+    for si, sy in enumerate(systems):
+        c = lib.Chi0.for_system(sy, precision=lib.CHI0_MIXED_BF16X3, stream=st, occ_drop_tol=1e-12)
+        c.load_system(sy)
+        mine = [k for k, (sj, _) in enumerate(probs) if sj == si]
+        for k in mine:
+            c.compute_rho(probs[k][1])
+            nts[k] = int(c.get_transitions().shape[0])
+            c.build_invert(probs[k][1], outs[k])
+        torch.cuda.synchronize(dev)
+        for k in mine:
+            pe[2 * k].record(stream)
+            c.compute_rho(probs[k][1])
+            c.build_invert(probs[k][1], outs[k])
+            pe[2 * k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        for k in mine:
+            per_problem[k] = pe[2 * k].elapsed_time(pe[2 * k + 1])
+        c.synchronize()
+        c.close()
+        torch.cuda.empty_cache()
+    seq_ms = sum(per_problem)
+    diff0 = ((outs[0] - keep).abs().pow(2).sum() / keep.abs().pow(2).sum()).sqrt().item()
+    flops = sum(chi0_flops(systems[si].ng, nts[k], systems[si].freqs.size) for k, (si, _) in enumerate(probs))
+    # the plain FP64 form of the first problem, for the speedup at the same size
     s0 = systems[0]
     c64 = lib.Chi0.for_system(s0, precision=lib.CHI0_FP64, stream=st, occ_drop_tol=1e-12)
     c64.load_system(s0)
@@ -554,31 +897,36 @@ def run_batching(args, rank, world, dist):
     c64.compute_rho(0)
     c64.build_invert(0, o64)
     torch.cuda.synchronize(dev)
-    e0.record(stream)
+    ev[0].record(stream)
     c64.compute_rho(0)
     c64.build_invert(0, o64)
-    e1.record(stream)
+    ev[1].record(stream)
     torch.cuda.synchronize(dev)
-    fp64_ms = e0.elapsed_time(e1)
-    err0 = ((o64 - outs[0]).abs().pow(2).sum() / o64.abs().pow(2).sum()).sqrt().item()
+    fp64_ms = ev[0].elapsed_time(ev[1])
+    err0 = ((o64 - keep).abs().pow(2).sum() / o64.abs().pow(2).sum()).sqrt().item()
     c64.close()
     if rank != 0:
         return
+    nq = [int(sy.q_frac.shape[0]) for sy in systems]
     line = {
         "metric": "batched chi0(q,w) + eps^-1 throughput (algorithmic Hermitian TFLOP/s)",
         "value": whole_job_tflops(world, flops, batch_ms), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)",
         "data": "synthetic",
-        "config": {"workload": "batching: 16 metallic systems (seeds 3000-3015; a 8-14 bohr, 4x4x4 k, 64 bands, "
-                               "400-4000 PW, N_G 200-1500, 8-64 imaginary GL frequencies, Fermi-Dirac 0.05 eV), "
-                               "the first q point of each", "problems": len(ctxs), "n_transitions": nts,
+        "config": {"workload": f"batching: {len(systems)} metallic systems (seeds 3000-{3000 + len(systems) - 1}; "
+                               "a 8-14 bohr, 4x4x4 k, 64 bands, 400-4000 PW, N_G 200-1500, 8-64 imaginary GL "
+                               "frequencies, Fermi-Dirac 0.05 eV), every q point of each",
+                   "problems": len(probs), "q_points_per_system": nq,
                    "ng": [sy.ng for sy in systems], "nw": [int(sy.freqs.size) for sy in systems],
+                   "n_transitions_total": int(sum(nts)), "helper_streams": args.batch_streams,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "batch_ms": batch_ms, "one_at_a_time_ms": seq_ms, "speedup_vs_one_at_a_time": seq_ms / batch_ms,
-        "rho_width": width, "problem_ms": per_problem,
-        "fp64_system0_ms": fp64_ms, "mixed_system0_ms": per_problem[0],
-        "speedup_vs_fp64_system0": fp64_ms / per_problem[0], "error_vs_fp64_system0": err0,
+        "batch_create_s": create_s, "rho_width": width, "tuned_contraction_ms": tuned_ms,
+        "problems_per_stream": [streams_of.count(h) for h in range(args.batch_streams)],
+        "batch_vs_one_at_a_time_problem0": diff0,
+        "fp64_problem0_ms": fp64_ms, "mixed_problem0_ms": per_problem[0],
+        "speedup_vs_fp64_problem0": fp64_ms / per_problem[0], "error_vs_fp64_problem0": err0,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -598,6 +946,9 @@ def main():
                     help="mixed: FP32 rho, BF16x3 tensor-core chi0, FP64 Dyson (default); "
                          "fp64: the plain FP64 form of every step, for the speedup comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain FP64 form and the error against the oracle")
+    ap.add_argument("--fp64-nw", type=int, default=2, help="frequencies of the plain FP64 form's timed step")
     ap.add_argument("--real-axis", action="store_true",
                     help="real frequencies on (0, 100] eV with 0.1 eV broadening (two contractions each, "
                          "general Dyson step)")
@@ -611,7 +962,10 @@ def main():
                                           "on the real-axis eps~^-1 of --ppa or --real-axis")
     ap.add_argument("--sigma-steps", type=int, default=2)
     ap.add_argument("--batching", action="store_true",
-                    help="the batching workload (16 metallic systems, one q each) in one batch, against one at a time")
+                    help="the batching workload (16 metallic systems, every q point) in one batch, against one at a time")
+    ap.add_argument("--batch-systems", type=int, default=16, help="systems of the batching workload (from the first)")
+    ap.add_argument("--batch-nq", type=int, default=None, help="keep only the first NQ q points of each system")
+    ap.add_argument("--batch-streams", type=int, default=4, help="helper streams of the batch")
     args = ap.parse_args()
     if args.ppa and (args.real_axis or args.ppa < 0):
         ap.error("--ppa takes a positive count and excludes --real-axis")

@@ -255,28 +255,50 @@ chi0_status chi0_invert_eps_noalloc(const void* chi0, const double* v_sqrt, int 
  * The paper spreads the response function over q points and transitions
  * (Parallelism section, linear response) and notes that q points are uneven
  * because the number of transitions varies.  A batch runs many independent
- * problems -- n contexts, each at its own q index iqs[i] -- as one unit: all
- * host set-up at creation, the oscillator strengths of every problem in one
- * persistent launch over a device task table, the remaining kernels of the
- * problems on `nstreams` helper streams, everything captured once into a CUDA
- * graph that each chi0_batch_run replays.  The rho tile width is timed on the
- * batch's own data at creation and remembered per geometry in the process.
+ * problems -- problem i is context ctxs[i] at q index iqs[i] -- as one unit.
+ * A context may appear several times with different q indices (every q point
+ * of one system): its problems share its coefficients and its mixed grids,
+ * which are computed once per replay.  At creation: all host set-up; the
+ * problems' remaining work is assigned to `nstreams` helper streams, longest
+ * first, each to the stream with the least estimated work, and the problems
+ * of one stream share one set of scratch buffers (operands, partials, chi0,
+ * Dyson panels) sized for the largest of them; the rho tile width and every
+ * contraction's transition split are timed on the batch's own data and the
+ * fastest kept.  Every replay runs the oscillator strengths of all problems
+ * in ONE persistent launch over a device task table, the rest on the helper
+ * streams, all captured once into a CUDA graph.
+ *   chi_out: NULL, or n device pointers to [nw_i][ng_i][ng_i] complex128
+ *            receiving chi0 of each problem (NULL entries: not returned);
  *   eps_out: NULL, or n device pointers to [nw_i][ng_i][ng_i] complex128
  *            receiving eps~^-1 of each problem (NULL entries skip the Dyson
- *            step of that problem); chi0 of problem i stays in its context.
- * All contexts must share one precision and be distinct; their wavefunctions
- * and energies must be set.  While the batch exists, call no other entry
- * point that computes on its contexts (they own the buffers the graph uses).
- * Errors: CHI0_EINVAL, CHI0_ESTATE, CHI0_EUNSUPPORTED (mixed precisions, or a
- * problem too large for one persistent launch), CHI0_ENOMEM, CHI0_ECUDA. */
+ *            step of that problem).  Each problem needs at least one output.
+ * The batch keeps its own q-point state and scratch: the contexts are read
+ * (inputs only) and may be used for other calls, but their wavefunctions and
+ * energies must not change, and the contexts must not be destroyed, while
+ * the batch exists (it reads their input buffers in place).  All contexts must share
+ * one precision.  The output pointers are captured into the graph: they must
+ * stay valid while the batch exists.
+ * Errors: CHI0_EINVAL (NULL, a repeated (context, q) pair, a problem with no
+ * output, iq out of range), CHI0_ESTATE (inputs not set), CHI0_EUNSUPPORTED
+ * (mixed precisions, or a problem too large for one persistent launch),
+ * CHI0_ENOMEM, CHI0_ECUDA. */
 typedef struct chi0_batch chi0_batch;
 
-chi0_status chi0_batch_create(chi0_ctx* const* ctxs, const int* iqs, void* const* eps_out, int n,
-                              int nstreams, chi0_batch** out);
+chi0_status chi0_batch_create(chi0_ctx* const* ctxs, const int* iqs, void* const* chi_out, void* const* eps_out,
+                              int n, int nstreams, chi0_batch** out);
 
 /* Replay the batch on `stream` (asynchronous; the first call captures the
- * graph).  Device-side errors are read with chi0_synchronize on a context. */
+ * graph).  Device-side errors are read with chi0_batch_synchronize. */
 chi0_status chi0_batch_run(chi0_batch* b, void* stream);
+
+/* Wait for the batch's work on every helper stream and report device-side
+ * errors of any problem (CHI0_ETIMEOUT, CHI0_ENOTPD, CHI0_ECUDA). */
+chi0_status chi0_batch_synchronize(chi0_batch* b);
+
+/* The schedule chosen at creation: stream_of (NULL or [n]) receives the
+ * helper stream of each problem; tuned_split_ms (NULL or one double) the
+ * summed time of the fastest split of each contraction during the tuning. */
+chi0_status chi0_batch_info(const chi0_batch* b, int* stream_of, double* tuned_split_ms);
 
 /* m bands per block chosen for the persistent rho launch (1, 2 or 4). */
 int chi0_batch_rho_width(const chi0_batch* b);

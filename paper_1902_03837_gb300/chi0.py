@@ -30,6 +30,7 @@ EXPORTS = (
     "chi0_invert_eps_noalloc", "chi0_mlp_nparams", "chi0_mlp_workspace_floats", "chi0_mlp_loss_grad",
     "chi0_mlp_adam", "chi0_mlp_predict", "chi0_term_features", "chi0_set_terminator", "chi0_set_bg_terminator",
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
+    "chi0_batch_synchronize", "chi0_batch_info",
     "chi0_ppa_fit", "chi0_ppa_eval", "chi0_build_sigma_i", "chi0_set_pole_grouping", "chi0_set_double_grid",
     "chi0_check_bounded_wait",
 )
@@ -94,7 +95,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_term_features.argtypes = [P, I, P, P, P, P, P]
     lib.chi0_set_terminator.argtypes = [P, P, I]
     lib.chi0_set_bg_terminator.argtypes = [P, I, D]
-    lib.chi0_batch_create.argtypes = [P, P, P, I, I, ctypes.POINTER(P)]
+    lib.chi0_batch_create.argtypes = [P, P, P, P, I, I, ctypes.POINTER(P)]
+    lib.chi0_batch_synchronize.argtypes = [P]
+    lib.chi0_batch_info.argtypes = [P, P, P]
     lib.chi0_batch_run.argtypes = [P, P]
     lib.chi0_batch_rho_width.argtypes = [P]
     lib.chi0_batch_destroy.argtypes = [P]
@@ -179,23 +182,44 @@ def ppa_eval(omega_t, R, freqs, eta, out, stream=None):
 
 
 class Batch:
-    """chi0_batch: many (context, q index) problems run as one captured graph."""
+    """chi0_batch: many (context, q index) problems run as one captured graph.
+    A context may appear with several q indices (they share its mixed grids).
+    eps_out / chi_out: per problem a complex128 CUDA tensor [nw][ng][ng] or
+    None; each problem needs at least one of them."""
 
-    def __init__(self, ctxs, iqs, eps_out=None, nstreams=4):
+    def __init__(self, ctxs, iqs, eps_out=None, nstreams=4, chi_out=None):
         n = len(ctxs)
         self._ctxs = list(ctxs)          # keep the contexts alive
         self._outs = list(eps_out) if eps_out is not None else None
+        self._chis = list(chi_out) if chi_out is not None else None
+        self.n = n
         hs = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
         qs = (ctypes.c_int * n)(*[int(q) for q in iqs])
-        outs = None
+        outs = chis = None
         if eps_out is not None:
             outs = (ctypes.c_void_p * n)(*[(_dev(o) if o is not None else None) for o in eps_out])
+        if chi_out is not None:
+            chis = (ctypes.c_void_p * n)(*[(_dev(o) if o is not None else None) for o in chi_out])
         h = ctypes.c_void_p()
-        st = _lib.chi0_batch_create(hs, qs, outs, n, int(nstreams), ctypes.byref(h))
+        st = _lib.chi0_batch_create(hs, qs, chis, outs, n, int(nstreams), ctypes.byref(h))
         if st != 0:
             raise Chi0Error(st, "chi0_batch_create failed: " +
-                            "; ".join(_lib.chi0_last_error(c.h).decode(errors="replace") for c in ctxs))
+                            "; ".join(_lib.chi0_last_error(c.h).decode(errors="replace") for c in ctxs[:1]))
         self.h = h
+
+    def synchronize(self):
+        st = _lib.chi0_batch_synchronize(self.h)
+        if st != 0:
+            raise Chi0Error(st, "chi0_batch_synchronize reported a device error")
+
+    def info(self):
+        """(helper stream of each problem, summed tuned contraction ms)."""
+        so = (ctypes.c_int * self.n)()
+        ms = ctypes.c_double()
+        st = _lib.chi0_batch_info(self.h, so, ctypes.byref(ms))
+        if st != 0:
+            raise Chi0Error(st, "chi0_batch_info failed")
+        return list(so), ms.value
 
     def run(self, stream=None):
         st = _lib.chi0_batch_run(self.h, stream)

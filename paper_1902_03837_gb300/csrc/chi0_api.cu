@@ -45,6 +45,8 @@ chi0_status cuda_fail(chi0_ctx* c, cudaError_t e, const char* what) {
 chi0_status ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return CHI0_OK;
+  if (b.borrowed)  // memory owned elsewhere cannot grow here
+    return fail(c, CHI0_ESTATE, "%s: shared buffer of %zu bytes, %zu needed", what, b.bytes, bytes);
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -97,9 +99,8 @@ chi0_status ctx_ensure(chi0_ctx* c, DevBuf& b, size_t bytes, const char* what) {
 namespace {
 
 void release(DevBuf& b) {
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
+  if (b.p && !b.borrowed) cudaFree(b.p);
+  b = DevBuf{};
 }
 
 size_t cplx_bytes(const chi0_ctx* c) { return c->fp64 ? 16 : 8; }
@@ -204,6 +205,10 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
   for (int ik = 0; ik < c->nk; ++ik)
     if (!c->wf_set[ik]) return fail(c, CHI0_ESTATE, "wavefunctions of k %d not set", ik);
   if (!c->energies_set) return fail(c, CHI0_ESTATE, "energies not set");
+  if (c->rho_planned_epoch == c->plan_epoch && c->plan_rho_iq == iq) {
+    c->rho_iq = c->chi_iq = c->eps_iq = -1;   // the plan holds; the results are stale
+    return CHI0_OK;
+  }
   chi0_status s;
   // ---- q-point setup on the host
   response_set(c, iq, c->h_gresp);
@@ -287,7 +292,11 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
   }
   c->rho_iq = c->chi_iq = c->eps_iq = -1;
   c->plan_rho_iq = iq;
-  if (c->nt == 0) return CHI0_OK;
+  if (c->nt == 0) {
+    c->rho_planned_epoch = c->plan_epoch;
+    ++c->rho_plan_serial;
+    return CHI0_OK;
+  }
   // ---- device buffers
   const size_t cb = cplx_bytes(c);
   const size_t ubytes = (size_t)c->nk * c->nb * g.N1 * g.NZ * g.N2 * cb;
@@ -340,6 +349,8 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
     a2.flops = (double)c->nt * g.N1 *
                (8.0 * g.N2 * g.HZ * g.NZ + ywork + 8.0 * g.ng);
   }
+  c->rho_planned_epoch = c->plan_epoch;
+  ++c->rho_plan_serial;
   return CHI0_OK;
 }
 
@@ -348,7 +359,7 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
 chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
   const int iq = c->plan_rho_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "rho not planned");
-  if (c->nt > 0) {
+  if (c->nt > 0 && !c->grid_shared) {
     const RhoGeom& g = c->geom;
     cudaError_t e;
     chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
@@ -362,6 +373,10 @@ chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
                                           (const float2*)c->d_tw2.p, (float2*)c->d_U.p, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
     chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
+  }
+  if (c->nt > 0) {
+    const RhoGeom& g = c->geom;
+    cudaError_t e;
     if (with_pairs) {
       chi0::stage_begin(c, CHI0_STAGE_RHO);
       if (c->fp64)
@@ -549,6 +564,8 @@ chi0_status launch_bg(chi0_ctx* c) {
 
 chi0_status plan_chi0(chi0_ctx* c, int iq) {
   if (iq != c->plan_rho_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
+  if (c->chi_planned_epoch == c->plan_epoch && c->plan_chi_iq == iq && c->chi_for_rho_serial == c->rho_plan_serial)
+    return CHI0_OK;
   const int nw0 = c->cfg.nw, ng = c->cfg.ng;
   // frequency list of the contraction (see chi0_ctx::nwv)
   c->h_vval.clear();
@@ -656,6 +673,25 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
     if (c->bg_on && (s = plan_bg(c)) != CHI0_OK) return s;
   }
   c->plan_chi_iq = iq;
+  c->chi_planned_epoch = c->plan_epoch;
+  c->chi_for_rho_serial = c->rho_plan_serial;
+  ++c->chi_plan_serial;
+  return CHI0_OK;
+}
+
+// the transition weights of every entry of the frequency list (a3)
+chi0_status launch_weights_stage(chi0_ctx* c) {
+  const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
+  chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
+  cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
+                                       (const double*)c->d_eps.p, (const double*)c->d_occ.p,
+                                       (const double*)c->d_omim.p, (const int*)c->d_vkind.p, c->nwv, c->cfg.eta,
+                                       pref, c->cfg.occ_drop_tol, c->bg_on, c->bg_eps,
+                                       c->grp_thresh > 0.0 ? (const double*)c->d_dpole.p : nullptr,
+                                       c->dg_nd > 0 ? (const double*)c->d_epsd.p : nullptr, c->dg_nd,
+                                       (double*)c->d_w.p, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
+  chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
   return CHI0_OK;
 }
 
@@ -671,17 +707,8 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
   } else {
     // the contraction's output: chi0 itself, or its parts H_r, H_i per real frequency
     double2* chiv = c->has_real ? (double2*)c->d_chiv.p : (double2*)c->d_chi.p;
-    const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
-    chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
-    cudaError_t e = chi0::launch_weights(c->nk, c->n_lo, c->Nn, c->Nm, c->nb, (const int32_t*)c->d_kq.p,
-                                         (const double*)c->d_eps.p, (const double*)c->d_occ.p,
-                                         (const double*)c->d_omim.p, (const int*)c->d_vkind.p, nw, c->cfg.eta,
-                                         pref, c->cfg.occ_drop_tol, c->bg_on, c->bg_eps,
-                                         c->grp_thresh > 0.0 ? (const double*)c->d_dpole.p : nullptr,
-                                         c->dg_nd > 0 ? (const double*)c->d_epsd.p : nullptr, c->dg_nd,
-                                         (double*)c->d_w.p, c->st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "weights launch");
-    chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+    if ((s = launch_weights_stage(c)) != CHI0_OK) return s;
+    cudaError_t e;
     c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
     c->stage[CHI0_STAGE_WEIGHTS].flops = 6.0 * (double)c->nt * nw;
     // chi0 algorithmic flops (Hermitian half): 4 ng (ng + 1) nt per frequency
@@ -733,6 +760,9 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
 
 chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
   if (iq != c->plan_chi_iq || iq < 0) return fail(c, CHI0_ESTATE, "chi0_build_chi0(%d) must come first", iq);
+  if (c->eps_planned_epoch == c->plan_epoch && c->plan_eps_iq == iq && c->plan_eps_out == A &&
+      c->eps_for_chi_serial == c->chi_plan_serial)
+    return CHI0_OK;
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   chi0_status s;
   if ((s = ensure(c, c->d_vsqrt, (size_t)ng * 8, "coulomb")) != CHI0_OK) return s;
@@ -777,6 +807,8 @@ chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
   }
   c->plan_eps_out = A;
   c->plan_eps_iq = iq;
+  c->eps_planned_epoch = c->plan_epoch;
+  c->eps_for_chi_serial = c->chi_plan_serial;
   return CHI0_OK;
 }
 
@@ -814,8 +846,9 @@ chi0_status launch_eps(chi0_ctx* c) {
   return CHI0_OK;
 }
 
-chi0_status launch_chi0_eps(chi0_ctx* c) {
+chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
   const int iq = c->plan_chi_iq;
+  if (copied) *copied = false;
   if (iq < 0 || c->plan_eps_iq != iq) return fail(c, CHI0_ESTATE, "build and Dyson step not planned");
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   chi0_status s;
@@ -877,6 +910,13 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
                                          c->s_dy);
     if (e != cudaSuccess) s = cuda_fail(c, e, "dyson launch");
     chi0::stage_end(c, CHI0_STAGE_DYSON, (general(w0) ? 1 : 2) + 3 * nT);
+    // a host output receives each group as soon as it is inverted, so that
+    // only the last group's copy follows the last contraction
+    if (s == CHI0_OK && host_out) {
+      e = cudaMemcpyAsync((char*)host_out + (size_t)w0 * n2 * 16, out, (size_t)gw * n2 * 16,
+                          cudaMemcpyDeviceToHost, c->s_dy);
+      if (e != cudaSuccess) s = cuda_fail(c, e, "eps copy out");
+    }
     w0 += gw;
   }
   c->st = base;
@@ -889,7 +929,48 @@ chi0_status launch_chi0_eps(chi0_ctx* c) {
   c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
   c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
   c->eps_iq = iq;
+  if (copied) *copied = host_out != nullptr;
   return CHI0_OK;
+}
+
+chi0_ctx* make_problem_ctx(const chi0_ctx* base) {
+  chi0_ctx* c = new (std::nothrow) chi0_ctx();
+  if (!c) return nullptr;
+  c->cfg = base->cfg;
+  c->q = base->q;
+  c->om = base->om;
+  c->cfg.q_frac = c->q.data();
+  c->cfg.omega = c->om.data();
+  c->nk = base->nk;
+  c->nb = base->nb;
+  c->npw_max = base->npw_max;
+  c->a = base->a;
+  c->omega_cell = base->omega_cell;
+  c->st = base->st;
+  c->fp64 = base->fp64;
+  c->h_npw = base->h_npw;
+  c->h_gvec = base->h_gvec;
+  c->wf_set = base->wf_set;
+  c->h_eps = base->h_eps;
+  c->h_occ = base->h_occ;
+  c->energies_set = base->energies_set;
+  const DevBuf* src[] = {&base->d_gvec, &base->d_npw, &base->d_coef, &base->d_eps, &base->d_occ, &base->d_epsd};
+  DevBuf* dst[] = {&c->d_gvec, &c->d_npw, &c->d_coef, &c->d_eps, &c->d_occ, &c->d_epsd};
+  for (int i = 0; i < 6; ++i) *dst[i] = DevBuf{src[i]->p, src[i]->bytes, true};
+  c->term_params = base->term_params;
+  c->term_bf16 = base->term_bf16;
+  c->bg_on = base->bg_on;
+  c->bg_eps = base->bg_eps;
+  c->grp_thresh = base->grp_thresh;
+  c->dg_nd = base->dg_nd;
+  return c;
+}
+
+std::vector<DevBuf*> scratch_slots(chi0_ctx* c) {
+  std::vector<DevBuf*> v = {&c->d_w, &c->d_part, &c->d_chi, &c->d_chiv, &c->d_colp, &c->d_rowp, &c->d_pinv,
+                            &c->d_termx, &c->d_termy};
+  for (DevBuf* b : tc_scratch_slots(c)) v.push_back(b);
+  return v;
 }
 
 }  // namespace chi0
@@ -971,26 +1052,36 @@ chi0_status chi0_set_wavefunctions(chi0_ctx* c, int ik, int npw, const int32_t* 
   if ((s = ensure(c, c->d_npw, (size_t)c->nk * 4, "npw")) != CHI0_OK) return s;
   // Miller indices: keep a host copy (sphere extents, alias checks)
   int32_t* hg = c->h_gvec.data() + (size_t)ik * c->npw_max * 3;
+  std::vector<int32_t> incoming((size_t)npw * 3);
   if (on_device) {
-    CK(cudaMemcpyAsync(hg, gvec, (size_t)npw * 12, cudaMemcpyDeviceToHost, c->st), "gvec D2H");
+    CK(cudaMemcpyAsync(incoming.data(), gvec, (size_t)npw * 12, cudaMemcpyDeviceToHost, c->st), "gvec D2H");
     CK(cudaStreamSynchronize(c->st), "synchronize");
   } else {
-    std::memcpy(hg, gvec, (size_t)npw * 12);
+    std::memcpy(incoming.data(), gvec, (size_t)npw * 12);
   }
-  std::memset(hg + (size_t)npw * 3, 0, (size_t)(c->npw_max - npw) * 12);
   for (int p = 0; p < npw * 3; ++p)
-    if (hg[p] < -1000 || hg[p] > 1000) return fail(c, CHI0_EINVAL, "Miller index out of range");
-  c->h_npw[ik] = npw;
-  CK(cudaMemcpyAsync((char*)c->d_gvec.p + (size_t)ik * c->npw_max * 12, hg,
-                     (size_t)c->npw_max * 12, cudaMemcpyHostToDevice, c->st),
-     "gvec H2D");
-  CK(cudaMemcpyAsync((char*)c->d_npw.p + (size_t)ik * 4, &c->h_npw[ik], 4, cudaMemcpyHostToDevice,
-                     c->st),
-     "npw H2D");
-  // coefficients: rows of npw, padded to npw_max
+    if (incoming[p] < -1000 || incoming[p] > 1000) return fail(c, CHI0_EINVAL, "Miller index out of range");
+  // a new sphere (or a first one) invalidates the plans; new coefficient
+  // values on the same sphere do not, and then the Miller indices and the
+  // zero padding on the device are already in place
+  const bool new_sphere =
+      !c->wf_set[ik] || c->h_npw[ik] != npw || std::memcmp(hg, incoming.data(), (size_t)npw * 12) != 0;
   const bool same = (coef_is_c64 != 0) == !c->fp64;
   char* dst = (char*)c->d_coef.p + (size_t)ik * c->nb * c->npw_max * cb;
-  CK(cudaMemsetAsync(dst, 0, (size_t)c->nb * c->npw_max * cb, c->st), "zero coefficients");
+  if (new_sphere) {
+    ++c->plan_epoch;
+    std::memcpy(hg, incoming.data(), (size_t)npw * 12);
+    std::memset(hg + (size_t)npw * 3, 0, (size_t)(c->npw_max - npw) * 12);
+    c->h_npw[ik] = npw;
+    CK(cudaMemcpyAsync((char*)c->d_gvec.p + (size_t)ik * c->npw_max * 12, hg,
+                       (size_t)c->npw_max * 12, cudaMemcpyHostToDevice, c->st),
+       "gvec H2D");
+    CK(cudaMemcpyAsync((char*)c->d_npw.p + (size_t)ik * 4, &c->h_npw[ik], 4, cudaMemcpyHostToDevice,
+                       c->st),
+       "npw H2D");
+    // coefficients: rows of npw, padded to npw_max
+    CK(cudaMemsetAsync(dst, 0, (size_t)c->nb * c->npw_max * cb, c->st), "zero coefficients");
+  }
   if (same) {
     CK(cudaMemcpy2DAsync(dst, (size_t)c->npw_max * cb, coef, (size_t)npw * cb, (size_t)npw * cb,
                          c->nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -1035,6 +1126,13 @@ chi0_status chi0_set_energies(chi0_ctx* c, const double* eps, const double* occ)
     if (!std::isfinite(eps[i])) return fail(c, CHI0_EINVAL, "non-finite energy at %zu", i);
     if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return fail(c, CHI0_EINVAL, "occupation outside [0,1] at %zu", i);
   }
+  // changed energies or occupations invalidate the plans (the transition
+  // set and the pole grouping are planned from them); unchanged ones are
+  // already on the device
+  if (c->energies_set && c->h_eps.size() == n && c->h_occ.size() == n &&
+      std::memcmp(c->h_eps.data(), eps, n * 8) == 0 && std::memcmp(c->h_occ.data(), occ, n * 8) == 0)
+    return CHI0_OK;
+  ++c->plan_epoch;
   c->h_eps.assign(eps, eps + n);
   c->h_occ.assign(occ, occ + n);
   chi0_status s;
@@ -1111,11 +1209,12 @@ chi0_status chi0_build_invert(chi0_ctx* c, int iq, void* chi_out, void* eps_out,
   }
   if ((s = chi0::plan_chi0(c, iq)) != CHI0_OK) return s;
   if ((s = chi0::plan_eps(c, iq, A)) != CHI0_OK) return s;
-  if ((s = chi0::launch_chi0_eps(c)) != CHI0_OK) return s;
+  bool copied = false;
+  if ((s = chi0::launch_chi0_eps(c, out_on_device ? nullptr : eps_out, &copied)) != CHI0_OK) return s;
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (chi_out) CK(cudaMemcpyAsync(chi_out, c->d_chi.p, bytes, kind, c->st), "chi0 copy out");
   if (!out_on_device) {
-    CK(cudaMemcpyAsync(eps_out, A, bytes, cudaMemcpyDeviceToHost, c->st), "eps copy out");
+    if (!copied) CK(cudaMemcpyAsync(eps_out, A, bytes, cudaMemcpyDeviceToHost, c->st), "eps copy out");
     CK(cudaStreamSynchronize(c->st), "synchronize");
     return check_device_error(c);
   }
@@ -1129,6 +1228,7 @@ chi0_status chi0_set_bg_terminator(chi0_ctx* c, int on, double eps_bar) {
     return fail(c, CHI0_EINVAL, "the learned terminator is set: the two corrections exclude each other");
   c->bg_on = on ? 1 : 0;
   c->bg_eps = eps_bar;
+  ++c->plan_epoch;
   // the transition block changes (every band n): compute_rho must run again
   c->rho_iq = c->chi_iq = c->eps_iq = -1;
   c->plan_rho_iq = c->plan_chi_iq = c->plan_eps_iq = -1;
@@ -1264,6 +1364,7 @@ chi0_status chi0_set_pole_grouping(chi0_ctx* c, double eps_thresh) {
     return fail(c, CHI0_EINVAL, "degeneracy threshold must be finite and >= 0");
   if (eps_thresh > 0.0 && c->dg_nd > 0)
     return fail(c, CHI0_EINVAL, "the double grid is set: pole grouping and the double grid exclude each other");
+  if (eps_thresh != c->grp_thresh) ++c->plan_epoch;
   c->grp_thresh = eps_thresh;
   return CHI0_OK;
 }
@@ -1273,6 +1374,7 @@ chi0_status chi0_set_double_grid(chi0_ctx* c, int nd, const double* eps_dense) {
   if (nd < 0 || nd > 4096 || (nd > 0 && !eps_dense)) return fail(c, CHI0_EINVAL, "nd out of range or NULL energies");
   if (nd > 0 && c->grp_thresh > 0.0)
     return fail(c, CHI0_EINVAL, "pole grouping is set: pole grouping and the double grid exclude each other");
+  ++c->plan_epoch;
   if (nd == 0) {
     c->dg_nd = 0;
     return CHI0_OK;

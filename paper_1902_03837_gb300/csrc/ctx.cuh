@@ -14,6 +14,7 @@ using chi0::RhoGeom;
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool borrowed = false;  // memory owned elsewhere (shared inputs, a batch's scratch): never freed here
 };
 
 struct chi0_ctx {
@@ -38,6 +39,21 @@ struct chi0_ctx {
   int rho_iq = -1, chi_iq = -1, eps_iq = -1;      // completed (launched) steps
   int plan_rho_iq = -1, plan_chi_iq = -1, plan_eps_iq = -1;  // planned steps
   double2* plan_eps_out = nullptr;
+  // batch problems: grid_shared = the mixed grids d_U belong to another
+  // problem of the same system (launch_rho then skips the wavefunction
+  // transforms); group_cap > 0 limits the frequencies per operand-split pass
+  bool grid_shared = false;
+  int group_cap = 0;
+  // Plan reuse: a plan stays valid while nothing it was made from changes.
+  // plan_epoch advances whenever an input that shapes a plan changes (Miller
+  // indices or sphere sizes, energies or occupations, and the settings of the
+  // corrections); each plan records the epoch it was made at and the serial
+  // number of the plan it builds on, so repeated steps over new coefficient
+  // values skip the host set-up and its synchronisation.
+  uint64_t plan_epoch = 1;
+  uint64_t rho_planned_epoch = 0, chi_planned_epoch = 0, eps_planned_epoch = 0;
+  uint64_t rho_plan_serial = 0, chi_plan_serial = 0;
+  uint64_t chi_for_rho_serial = 0, eps_for_chi_serial = 0;
   bool capturing = false;  // inside a CUDA graph capture: no event timers
   std::vector<int32_t> h_gresp;  // [ng][3] of rho_iq
   std::vector<int32_t> h_kq, h_g0;
@@ -145,11 +161,26 @@ cudaError_t mlp_predict(const float* prm, const float* x, int64_t batch, int bf1
                         cudaStream_t st);
 chi0_status term_plan(chi0_ctx* c, int iq);
 chi0_status term_launch(chi0_ctx* c, double2* chi);
+// Batch support: a problem context that shares the inputs (coefficients,
+// Miller indices, energies, occupations, dense-grid energies) of base by
+// borrowing its buffers, with its own q-point state; and the scratch buffers
+// of a planned context that a batch may replace by memory shared between the
+// problems that run one after the other on one stream (chi0_api.cu's slots
+// first, then the tensor-core state's).
+chi0_ctx* make_problem_ctx(const chi0_ctx* base);
+std::vector<DevBuf*> scratch_slots(chi0_ctx* c);
+std::vector<DevBuf*> tc_scratch_slots(chi0_ctx* c);
+// time the contraction of the first frequency for a few transition splits
+// and keep the fastest (needs R and the weights of the current plan; the
+// chunk-partial buffer must hold max_parts_factor times the planned partials)
+chi0_status tc_tune_split(chi0_ctx* c, float* best_ms);
 // plan (host set-up, allocation, uploads; may synchronise) and launch
 // (kernels only, capturable) halves of compute_rho / build_chi0 / invert_eps
 chi0_status plan_rho(chi0_ctx* c, int iq);
 chi0_status launch_rho(chi0_ctx* c, bool with_pairs);
 chi0_status plan_chi0(chi0_ctx* c, int iq);
+// the weights kernel of the planned frequency list (part of launch_chi0)
+chi0_status launch_weights_stage(chi0_ctx* c);
 // defer_combine leaves the real-axis frequencies as their parts H_r, H_i
 // (the caller combines them, frequency group by group)
 chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq = nullptr,
@@ -160,5 +191,8 @@ chi0_status launch_eps(chi0_ctx* c);
 // overlaps the contraction of the later frequencies (mixed form without a
 // terminator; otherwise the two run one after the other).  Needs plan_chi0
 // and plan_eps.
-chi0_status launch_chi0_eps(chi0_ctx* c);
+// host_out (optional): a host buffer that receives eps~^-1 group by group on
+// the Dyson stream; *copied tells whether it was written (only the
+// overlapped pipeline does so)
+chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out = nullptr, bool* copied = nullptr);
 }  // namespace chi0

@@ -617,7 +617,10 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   chi0_status s;
   if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
-  const size_t nparts = std::max((size_t)t.nchunks * t.ntiles,
+  // a batch problem (group_cap > 0) keeps room for twice the planned
+  // partials, for the split candidates of tc_tune_split
+  const size_t room = c->group_cap > 0 ? 2 : 1;
+  const size_t nparts = std::max((size_t)t.nchunks * t.ntiles * room,
                                   c->has_real ? (size_t)t.nchunks_f * t.ntiles_f : (size_t)0);
   if ((s = ctx_ensure(c, t.part, nparts * (kBM / 2) * (kBN / 2) * 16, "chunk partials")) != CHI0_OK)
     return s;
@@ -632,6 +635,7 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     int have = 0;
     while (have < kPrepGroup && t.ah[have].bytes >= opb && t.al[have].bytes >= opb) ++have;
     int g = std::min(kPrepGroup, std::max(1, nw));
+    if (c->group_cap > 0) g = std::min(g, c->group_cap);
     while (g > std::max(1, have) && (double)(g - have) * 2.0 * (double)opb > 0.5 * (double)free_b) --g;
     t.group = g;
   }
@@ -779,13 +783,86 @@ void tc_release(chi0_ctx* c) {
   TcState* t = static_cast<TcState*>(c->tc);
   DevBuf* bufs[] = {&t->bh, &t->bl, &t->part};
   for (DevBuf* b : bufs)
-    if (b->p) cudaFree(b->p);
+    if (b->p && !b->borrowed) cudaFree(b->p);
   for (int g = 0; g < kPrepGroup; ++g) {
-    if (t->ah[g].p) cudaFree(t->ah[g].p);
-    if (t->al[g].p) cudaFree(t->al[g].p);
+    if (t->ah[g].p && !t->ah[g].borrowed) cudaFree(t->ah[g].p);
+    if (t->al[g].p && !t->al[g].borrowed) cudaFree(t->al[g].p);
   }
   delete t;
   c->tc = nullptr;
+}
+
+std::vector<DevBuf*> tc_scratch_slots(chi0_ctx* c) {
+  std::vector<DevBuf*> v;
+  if (!c->tc) c->tc = new TcState();
+  TcState& t = *static_cast<TcState*>(c->tc);
+  v.push_back(&t.bh);
+  v.push_back(&t.bl);
+  v.push_back(&t.part);
+  for (int g = 0; g < kPrepGroup; ++g) {
+    v.push_back(&t.ah[g]);
+    v.push_back(&t.al[g]);
+  }
+  return v;
+}
+
+// The contraction of the first entry of the frequency list (its operands
+// split as tc_launch does) timed for the planned transition split and for
+// half and twice as many splits; the fastest is kept for the later launches.
+chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
+  if (!c->tc || c->nt == 0) return CHI0_OK;
+  TcState& t = *static_cast<TcState*>(c->tc);
+  const int ng = c->cfg.ng;
+  const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
+  PrepOut ob{};
+  ob.hi[0] = (__nv_bfloat16*)t.bh.p;
+  ob.lo[0] = (__nv_bfloat16*)t.bl.p;
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, ob);
+  PrepOut oa{};
+  oa.hi[0] = (__nv_bfloat16*)t.ah[0].p;
+  oa.lo[0] = (__nv_bfloat16*)t.al[0].p;
+  oa.wr[0] = (const double*)c->d_w.p;
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, oa);
+  const size_t cap = t.part.bytes / ((size_t)(kBM / 2) * (kBN / 2) * 16);
+  const int base_split = (t.total_kb + t.kbpc - 1) / t.kbpc;
+  int best_kbpc = t.kbpc, best_n = t.nchunks;
+  float best = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, CHI0_ECUDA, "events for the split tuning");
+  }
+  for (int sp : {base_split, std::max(1, base_split / 2), 2 * base_split}) {
+    const int kbpc = (t.total_kb + sp - 1) / sp;
+    const int nchunks = (t.total_kb + kbpc - 1) / kbpc;
+    if ((size_t)nchunks * t.ntiles > cap) continue;
+    const int nunits = t.ntiles * nchunks;
+    const unsigned grid = (unsigned)std::min(nunits, std::max(1, t.nsm));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // the first run warms the caches
+      cudaEventRecord(e0, c->st);
+      k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[0], t.m_al[0], t.m_bh, t.m_bl, t.total_kb, kbpc,
+                                                            t.mpad, (double2*)t.part.p, t.ntiles, nunits,
+                                                            (int*)c->d_err.p, 0, t.mpad, 0);
+      cudaEventRecord(e1, c->st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 1e30f;
+      }
+    }
+    if (ms < best) {
+      best = ms;
+      best_kbpc = kbpc;
+      best_n = nchunks;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  t.kbpc = best_kbpc;
+  t.nchunks = best_n;
+  if (best_ms) *best_ms = best;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CHI0_OK : ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
 }
 
 // ---- failure detection: the bounded wait ---------------------------------------

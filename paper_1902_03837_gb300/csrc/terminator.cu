@@ -451,6 +451,7 @@ chi0_status chi0_set_terminator(chi0_ctx* c, const float* params, int bf16) {
   c->term_params = params;
   c->term_bf16 = bf16;
   c->chi_iq = c->eps_iq = -1;
+  ++c->plan_epoch;
   return CHI0_OK;
 }
 

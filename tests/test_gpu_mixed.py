@@ -108,6 +108,15 @@ def test_precision_workload_full_size(lib):
     ctx.invert_eps(0, inv_d)
     ctx.synchronize()
     ctx.close()
+    # the Dyson step alone at N_G = 1000: the GPU's eps~^-1 against the
+    # oracle's Gauss-Jordan inversion of eps~ built from the GPU's own chi0
+    # (same input, so the comparison isolates the FP64 elimination)
+    qg = O.qg_norms(s.spec.a, s.q_frac[0], G)
+    for iw in (0, nw - 1):
+        want = O.eps_inv_gauss_jordan(chi_d[iw].cpu().numpy(), qg)
+        e_d = _rel(inv_d[iw].cpu().numpy(), want)
+        print(f"precision workload, eps~^-1 at N_G = 1000 vs oracle Gauss-Jordan (frequency {iw}): {e_d:.3e}")
+        assert e_d < 1e-10, (iw, e_d)
     # properties of the full matrices (any size)
     herm = (chi_d - chi_d.conj().transpose(1, 2)).abs().max().item()
     assert herm == 0.0
@@ -116,13 +125,25 @@ def test_precision_workload_full_size(lib):
     assert ev.max() < 1e-6 * scale  # negative semidefinite up to the mixed-precision error
     ev_inv = torch.linalg.eigvalsh(inv_d[[0, nw - 1]]).cpu().numpy()
     assert ev_inv.min() > 0.0 and ev_inv.max() < 1.0 + 1e-6
-    # the 64 x 64 sub-block against the oracle (all transitions)
-    sub = slice(0, 64)
-    got = chi_d[:, sub, sub].cpu().numpy()
-    ref = O.chi0_tr(s, 0, G[:64], s.freqs, s.eta)
+    # against the oracle (all transitions, all frequencies) on the G subset
+    # G_0..G_63 (tile (0, 0) of the real 2 N_G grid) plus G_496..G_511 and
+    # G_984..G_999: the entries among them fall in the diagonal tiles 0, 7 and
+    # 15, in the off-diagonal tiles (7, 0), (15, 0), (15, 7) of the lower
+    # triangle and in their Hermitian mirrors above the diagonal
+    sub = np.concatenate([np.arange(0, 64), np.arange(496, 512), np.arange(984, 1000)])
+    idx = torch.as_tensor(sub, device="cuda")
+    got = chi_d[:, idx][:, :, idx].cpu().numpy()
+    ref = O.chi0_tr(s, 0, G[sub], s.freqs, s.eta)
     e = _rel(got, ref)
     assert e < TOL, e
     per_w = [_rel(got[i], ref[i]) for i in range(nw)]
-    print(f"precision workload, 64 x 64 sub-block: chi0 relative Frobenius error {e:.3e} "
+    print(f"precision workload, 96 x 96 G subset: chi0 relative Frobenius error {e:.3e} "
           f"(worst frequency {max(per_w):.3e})")
     assert max(per_w) < TOL, per_w
+    # each block of the subset on its own (the small corner blocks carry
+    # little of the Frobenius norm, so they are checked separately)
+    parts = [np.arange(0, 64), np.arange(64, 80), np.arange(80, 96)]
+    for a in parts:
+        for b in parts:
+            e_ab = _rel(got[:, a][:, :, b], ref[:, a][:, :, b])
+            assert e_ab < TOL, (a[0], b[0], e_ab)

@@ -87,3 +87,47 @@ def test_build_invert_validation(lib):
     with pytest.raises(ValueError):
         ctx.build_invert(0, out, np.zeros((s.freqs.size, s.ng, s.ng), np.complex128))
     ctx.close()
+
+
+def _fresh(lib, s, prec, stream):
+    import torch
+    ctx = lib.Chi0.for_system(s, precision=prec, stream=stream)
+    ctx.load_system(s)
+    ctx.compute_rho(0)
+    inv = torch.zeros((s.freqs.size, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    chi = torch.zeros_like(inv)
+    ctx.build_invert(0, inv, chi)
+    ctx.synchronize()
+    ctx.close()
+    return chi, inv
+
+
+@pytest.mark.parametrize("prec,dtype", [(1, "c64"), (0, "c128")])
+def test_plans_reused_only_while_valid(lib, prec, dtype):
+    """A context reuses its plans across steps whose inputs differ only in the
+    coefficient values (same spheres, energies and occupations), and plans
+    again when the spheres or the occupations change.  Every step must equal
+    a fresh context on the same inputs, bit for bit."""
+    import dataclasses
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    a = _system(dtype)
+    b = make_system(dataclasses.replace(a.spec, seed=72))     # same spheres, new coefficients
+    b.eps, b.occ = a.eps.copy(), a.occ.copy()                  # and the same energies
+    c = make_system(dataclasses.replace(a.spec, seed=73, n_occ=4))            # other occupations
+    d = make_system(dataclasses.replace(a.spec, seed=74, kc=a.spec.kc * 0.93))  # other spheres
+    assert np.array_equal(a.gvec, b.gvec) and not np.array_equal(a.coef, b.coef)
+    assert not np.array_equal(a.occ, c.occ) and not np.array_equal(a.npw, d.npw)
+    ctx = lib.Chi0.for_system(a, precision=prec, stream=stream)
+    shape = (a.freqs.size, a.ng, a.ng)
+    for s in (a, b, b, c, a, d):
+        ctx.load_system(s)
+        ctx.compute_rho(0)
+        inv = torch.full(shape, complex(float("nan"), 0.0), dtype=torch.complex128, device="cuda")
+        chi = torch.full_like(inv, complex(float("nan"), 0.0))
+        ctx.build_invert(0, inv, chi)
+        ctx.synchronize()
+        want_chi, want_inv = _fresh(lib, s, prec, stream)
+        assert torch.equal(chi, want_chi)
+        assert (inv - want_inv).abs().max().item() <= 1e-13 * want_inv.abs().max().item()
+    ctx.close()
