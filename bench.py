@@ -813,6 +813,285 @@ def baseline_and_error(s, nt, jobs, cmp_data, fp64_line):
     return base, err
 
 
+def large_states_device(spec, dev):
+    """The states of the large workload generated on the device, k point by k
+    point, by the recipe of synth.make_system: complex Gaussian draws keyed by
+    (seed, k) (torch's Philox generator on the GPU instead of numpy's PCG64),
+    orthonormalised per k by QR (cuSOLVER through torch.linalg.qr, FP32), the
+    time-reversal partner -k derived by conjugation, c_{k'}(G) =
+    conj(c_k(-G - G1)), and self-partner k points orthonormalised in real
+    coordinates so that c(G) = conj(c(-G - 2k)) holds exactly.  Yields
+    (ik, gvec [npw][3] int32, coef [nbands][npw] complex64), both on dev."""
+    import math
+    import torch
+    from synth import kgrid_fractions, sphere_miller, tr_partner
+    kgrid = tuple(int(v) for v in spec.kgrid)
+    nk = kgrid[0] * kgrid[1] * kgrid[2]
+    nb = spec.n_bands
+    kfrac = kgrid_fractions(kgrid)
+    gen = torch.Generator(device=dev)
+    done = np.zeros(nk, dtype=bool)
+
+    def sphere(ik):
+        g = sphere_miller(kfrac[ik], spec.a, spec.kc)
+        return g, torch.from_numpy(np.ascontiguousarray(g)).to(dev)
+
+    for ik in range(nk):
+        if done[ik]:
+            continue
+        jk = tr_partner(ik, kgrid)
+        g, g_d = sphere(ik)
+        gen.manual_seed(spec.seed * 1000003 + ik)
+        if jk == ik:
+            two_k = np.rint(2.0 * kfrac[ik]).astype(np.int64)
+            where = {tuple(v): p for p, v in enumerate(g.tolist())}
+            partner = np.array([where[tuple((-v - two_k).tolist())] for v in g.astype(np.int64)])
+            idx = np.arange(g.shape[0])
+            fixed = np.nonzero(partner == idx)[0]
+            reps = np.nonzero(partner > idx)[0]
+            nf, nr = fixed.size, reps.size
+            x = torch.randn((nf + 2 * nr, nb), generator=gen, device=dev, dtype=torch.float32)
+            q = torch.linalg.qr(x, mode="reduced")[0]
+            c = torch.zeros((nb, g.shape[0]), dtype=torch.complex64, device=dev)
+            s2 = 1.0 / math.sqrt(2.0)
+            xr, yr = q[nf:nf + nr].T, q[nf + nr:].T
+            c[:, torch.from_numpy(fixed).to(dev)] = q[:nf].T.to(torch.complex64)
+            c[:, torch.from_numpy(reps).to(dev)] = torch.complex(s2 * xr, s2 * yr)
+            c[:, torch.from_numpy(partner[reps]).to(dev)] = torch.complex(s2 * xr, -s2 * yr)
+            done[ik] = True
+            yield ik, g_d, c
+            continue
+        z = torch.randn((g.shape[0], nb), generator=gen, device=dev, dtype=torch.complex64)
+        c = torch.linalg.qr(z, mode="reduced")[0].T.contiguous()
+        yield ik, g_d, c
+        g1 = np.rint(kfrac[ik] + kfrac[jk]).astype(np.int64)
+        gp, gp_d = sphere(jk)
+        where = {tuple(v): p for p, v in enumerate(g.tolist())}
+        src = np.array([where[tuple((-v - g1).tolist())] for v in gp.astype(np.int64)], dtype=np.int64)
+        yield jk, gp_d, c[:, torch.from_numpy(src).to(dev)].conj().contiguous()
+        done[ik] = done[jk] = True
+
+
+def run_large(args, rank, world, dist):
+    """The large workload (12x12x12 k, 24 + 976 bands, ~4000 PW, FFT 72^3,
+    N_G = 3000, 64 imaginary frequencies) at one q point: the transitions
+    (40.5 million; rho alone would be 971 GB) streamed in band blocks through
+    rho, the operand split and the contraction, chi0 summed in FP64, then the
+    FP64 Dyson step.  One step is the whole q point; it runs in minutes, so
+    the warm-up is a step of a smaller k grid of the same system shape."""
+    import dataclasses
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1902_03837_gb300 import chi0 as lib
+    from synth import cfg_large, large_energies, sphere_miller, kgrid_fractions
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    spec = cfg_large(kgrid=tuple(args.kgrid) if args.kgrid else (12, 12, 12), nw=args.nw if args.nw != 32 else 64)
+    iq = args.large_iq
+    spec = dataclasses.replace(spec, q_frac=(spec.q_frac[iq],))
+
+    def make_ctx(sp):
+        kf = kgrid_fractions(sp.kgrid)
+        npw_max = max(sphere_miller(kf[k], sp.a, sp.kc).shape[0] for k in range(kf.shape[0]))
+        ctx = lib.Chi0(a=sp.a, kgrid=sp.kgrid, nbands=sp.n_bands, npw_max=npw_max, fft=sp.fft, ng=sp.ng,
+                       q_frac=np.array(sp.q_frac), omega=np.array(sp.freqs), eta=sp.eta,
+                       spin_factor=sp.spin_factor, precision=lib.CHI0_MIXED_BF16X3, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        npw = []
+        for ik, gv, cf in large_states_device(sp, dev):
+            ctx.set_wavefunctions(ik, gv, cf)
+            npw.append(int(gv.shape[0]))
+        eps = large_energies(sp)
+        occ = np.zeros_like(eps)
+        occ[:, :sp.n_occ] = 1.0
+        ctx.set_energies(eps, occ)
+        ctx.synchronize()
+        ctx.set_band_blocks(args.large_bands, args.large_kblock)
+        return ctx, time.perf_counter() - t0, npw_max, float(np.mean(npw))
+
+    ng, nw = spec.ng, len(spec.freqs)
+    inv = torch.empty((nw, ng, ng), dtype=torch.complex128, device=dev)
+    # warm-up: the same shape on a 2x2x2 k grid (kernels, plans, clocks)
+    wctx, _, _, _ = make_ctx(dataclasses.replace(spec, kgrid=(2, 2, 2), q_frac=((0.5, 0.0, 0.0),)))
+    for _ in range(max(1, args.warmup)):
+        wctx.compute_rho(0)
+        wctx.build_invert(0, inv)
+    wctx.synchronize()
+    wctx.close()
+    torch.cuda.empty_cache()
+    ctx, gen_s, npw_max, npw_mean = make_ctx(spec)
+    ctx.get_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.compute_rho(0)
+            ctx.build_invert(0, inv)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ctx.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    st_ms, st_bytes, st_flops, launches = ctx.get_stats()
+    nt = int(ctx.get_transitions().shape[0])
+    spectrum = torch.linalg.eigvalsh(inv[[0, nw - 1]]).cpu().numpy()
+    ctx.close()
+    if rank != 0:
+        return
+    pk = peaks()
+    flops = chi0_flops(ng, nt, nw)
+    per = {k: v / args.steps for k, v in st_ms.items()}
+    cargs = argparse.Namespace(precision="mixed", steps=args.steps)
+    stages = stage_rooflines(cargs, st_ms, st_bytes, st_flops, pk, nt, ng, nw)
+    con = stages.get("contract", {})
+    line = {
+        "metric": METRIC, "value": whole_job_tflops(world, flops, ms), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3/fp32 (chi0), fp32 (rho), f64 (eps^-1)", "data": "synthetic",
+        "config": {"workload": f"large: a=10 bohr, k {'x'.join(map(str, spec.kgrid))}, 24+976 bands, ~4000 PW "
+                               f"(mean {npw_mean:.0f}, max {npw_max}), FFT 72^3, N_G=3000, {nw} imaginary GL "
+                               f"frequencies in [0,100] eV, q = ({spec.q_frac[0][0]:.4f},0,0), complex64",
+                   "n_transitions": nt, "band_blocks": [args.large_bands, args.large_kblock],
+                   "l2": "inputs larger than L2", "warmup_note": "warm-up steps on a 2x2x2 k grid of the same shape",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "input_generation_s": gen_s, "stage_ms_per_step": per, "stage_roofline": stages,
+        "roofline": {"kernel": "k_herk_bf16x3", "stage": "contract", "bound": "tensor",
+                     "achieved": con.get("tflops"), "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                     "frac": con.get("tensor_frac"), "peak_source": f"BF16 dense sustained ({pk['source']})",
+                     "traffic": None, "traffic_source": "not captured for this workload"},
+        "eps_inv_spectrum_w0_wlast": [float(spectrum.min()), float(spectrum.max())],
+        "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_terminator(args, rank, world, dist):
+    """The learned-terminator workload: systems of 6x6x6 k, 12 occupied bands,
+    ~1500 PW, FFT 32^3, N_G = 500, 16 imaginary frequencies, q = (1/6,0,0),
+    each with 800 bands (the full-band sum, the reference) and its first 100
+    (truncated).  The network is trained on the GPU by the library's kernels
+    on the pairs of the training systems (seeds 4000...) and judged on the
+    held-out ones (seeds 5000...) against the full-band sum, beside the
+    truncated sum alone and the Bruneval-Gonze extrapolar correction."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1902_03837_gb300 import chi0 as lib
+    from paper_1902_03837_gb300 import terminator as term
+    from synth import cfg_learned, large_energies, kgrid_fractions, sphere_miller, HA_EV
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    nb_t = args.term_truncated
+    spec0 = cfg_learned()
+    kf = kgrid_fractions(spec0.kgrid)
+    npw_max = max(sphere_miller(kf[k], spec0.a, spec0.kc).shape[0] for k in range(kf.shape[0]))
+
+    def ctx_for(nb):
+        return lib.Chi0(a=spec0.a, kgrid=spec0.kgrid, nbands=nb, npw_max=npw_max, fft=spec0.fft, ng=spec0.ng,
+                        q_frac=np.array(spec0.q_frac), omega=np.array(spec0.freqs), eta=spec0.eta,
+                        spin_factor=spec0.spin_factor, precision=lib.CHI0_MIXED_BF16X3, stream=st)
+
+    ctx_f, ctx_t = ctx_for(spec0.n_bands), ctx_for(nb_t)
+    nw, ng = len(spec0.freqs), spec0.ng
+    chi_f = torch.empty((nw, ng, ng), dtype=torch.complex128, device=dev)
+    chi_t = torch.empty_like(chi_f)
+
+    def load(seed, truncated):
+        """The system's states into the full-band context and the truncated ones."""
+        spec = cfg_learned(seed=seed)
+        for ik, gv, cf in large_states_device(spec, dev):
+            ctx_f.set_wavefunctions(ik, gv, cf)
+            ct = cf[:nb_t].contiguous()
+            for c in truncated:
+                c.set_wavefunctions(ik, gv, ct)
+        eps = large_energies(spec)
+        occ = np.zeros_like(eps)
+        occ[:, :spec.n_occ] = 1.0
+        ctx_f.set_energies(eps, occ)
+        for c in truncated:
+            c.set_energies(np.ascontiguousarray(eps[:, :nb_t]), np.ascontiguousarray(occ[:, :nb_t]))
+        return eps
+
+    t0 = time.perf_counter()
+    X, T = [], []
+    gpu_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for seed in range(4000, 4000 + args.term_train):
+        load(seed, [ctx_t])
+        e0.record(stream)
+        for c, out in ((ctx_f, chi_f), (ctx_t, chi_t)):
+            c.compute_rho(0)
+            c.build_chi0(0, out)
+        e1.record(stream)
+        n = chi_t.numel()
+        x = torch.empty((n, 5), dtype=torch.float32, device=dev)
+        t = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        ctx_t.term_features(0, chi_t, x, chi_f, t)
+        torch.cuda.synchronize(dev)
+        gpu_ms += e0.elapsed_time(e1)
+        X.append(x)
+        T.append(t)
+    X = torch.cat(X)
+    T = torch.cat(T)
+    t_data = time.perf_counter() - t0
+    e0.record(stream)
+    params, hist = term.train(X, T, steps=args.term_steps, batch=4096, lr=2e-3, seed=1, stream=st,
+                              log_every=max(1, args.term_steps // 10))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    train_ms = e0.elapsed_time(e1)
+    del X, T
+    torch.cuda.empty_cache()
+    # held-out systems: truncated, truncated + network, truncated + extrapolar correction
+    ctx_c = ctx_for(nb_t)
+    ctx_c.set_terminator(params, True)
+    ctx_b = ctx_for(nb_t)
+    chi_c = torch.empty_like(chi_f)
+    errs = {"truncated": [], "truncated_plus_network": [], "truncated_plus_bg_1.5Ha": [],
+            "truncated_plus_bg_mean_omitted": []}
+    for seed in range(5000, 5000 + args.term_test):
+        eps = load(seed, [ctx_t, ctx_c, ctx_b])
+        for c, out in ((ctx_f, chi_f), (ctx_t, chi_t), (ctx_c, chi_c)):
+            c.compute_rho(0)
+            c.build_chi0(0, out)
+        nf = torch.linalg.norm(chi_f).item()
+        errs["truncated"].append(torch.linalg.norm(chi_t - chi_f).item() / nf)
+        errs["truncated_plus_network"].append(torch.linalg.norm(chi_c - chi_f).item() / nf)
+        for key, eb in (("truncated_plus_bg_1.5Ha", 1.5), ("truncated_plus_bg_mean_omitted",
+                                                             float(eps[:, nb_t:].mean()))):
+            ctx_b.set_bg_terminator(eb)
+            ctx_b.compute_rho(0)
+            ctx_b.build_chi0(0, chi_c)
+            errs[key].append(torch.linalg.norm(chi_c - chi_f).item() / nf)
+        ctx_b.set_bg_terminator(1.5, on=False)
+    for c in (ctx_f, ctx_t, ctx_c, ctx_b):
+        c.synchronize()
+        c.close()
+    if rank != 0:
+        return
+    summary = {k: {"mean": float(np.mean(v)), "std": float(np.std(v)), "max": float(np.max(v))}
+               for k, v in errs.items()}
+    line = {
+        "metric": "learned band-sum terminator: held-out relative Frobenius error of chi0 against the full-band sum",
+        "value": summary["truncated_plus_network"]["mean"], "unit": "relative error", "higher_is_better": False,
+        "n_gpus": world, "steps": args.term_steps, "warmup": 0, "dtype": "bf16 network, bf16x3/fp32 chi0",
+        "data": "synthetic", "vs_baseline": None, "scaling": "weak",
+        "config": {"workload": f"learned terminator: 6x6x6 k, 12 occupied, {nb_t} of 800 bands, ~1500 PW, FFT 32^3, "
+                               f"N_G=500, 16 imaginary GL frequencies, q=(1/6,0,0); {args.term_train} training "
+                               f"systems (seeds 4000..), {args.term_test} held-out (seeds 5000..)",
+                   "network": "5 -> 128 -> 128 -> 2 tanh, BF16 operands, FP32 accumulation, Adam lr 2e-3, "
+                              f"batch 4096, {args.term_steps} steps"},
+        "held_out_error": summary, "held_out_per_system": errs,
+        "loss_history": hist, "data_seconds": t_data, "chi0_pairs_gpu_ms": gpu_ms, "train_ms": train_ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batching(args, rank, world, dist):
     """The batching workload: 16 seeded metallic systems of different sizes,
     every q point of each (4-20 per system, 200 problems), all in one batch
@@ -966,6 +1245,17 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=16, help="systems of the batching workload (from the first)")
     ap.add_argument("--batch-nq", type=int, default=None, help="keep only the first NQ q points of each system")
     ap.add_argument("--batch-streams", type=int, default=4, help="helper streams of the batch")
+    ap.add_argument("--terminator", action="store_true",
+                    help="the learned-terminator workload: train on chi0 pairs, report the held-out error")
+    ap.add_argument("--term-train", type=int, default=200, help="training systems of the terminator workload")
+    ap.add_argument("--term-test", type=int, default=50, help="held-out systems of the terminator workload")
+    ap.add_argument("--term-steps", type=int, default=20000, help="Adam steps of the terminator training")
+    ap.add_argument("--term-truncated", type=int, default=100, help="bands of the truncated sum")
+    ap.add_argument("--workload", default="precision", choices=["precision", "large"],
+                    help="large: 12x12x12 k, 1000 bands, N_G 3000, 64 frequencies, one q point, band-block streamed")
+    ap.add_argument("--large-iq", type=int, default=0, help="q point (0..7) of the large workload")
+    ap.add_argument("--large-bands", type=int, default=122, help="n bands per block (large workload)")
+    ap.add_argument("--large-kblock", type=int, default=64, help="k points per block (large workload)")
     args = ap.parse_args()
     if args.ppa and (args.real_axis or args.ppa < 0):
         ap.error("--ppa takes a positive count and excludes --real-axis")
@@ -983,6 +1273,10 @@ def main():
         dist = tdist
     if args.batching:
         run_batching(args, rank, world, dist)
+    elif args.workload == "large":
+        run_large(args, rank, world, dist)
+    elif args.terminator:
+        run_terminator(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist is not None:

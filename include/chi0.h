@@ -191,6 +191,23 @@ chi0_status chi0_get_rho(chi0_ctx* ctx, void* out);
  * Synchronises.  Errors: CHI0_ESTATE, CHI0_EINVAL (row out of range), CHI0_ECUDA. */
 chi0_status chi0_get_rho_rows(chi0_ctx* ctx, const int64_t* rows, int64_t nrows, void* out);
 
+/* Band-block streaming for problems whose oscillator strengths do not fit in
+ * device memory (the paper distributes the response function's memory over
+ * the band indices: Parallelism section, linear response).  With
+ * bands_per_block > 0, chi0_compute_rho keeps only the mixed grids of the
+ * occupied-side bands m (at every k) and chi0_build_chi0 / chi0_build_invert
+ * take the transitions in blocks of k_per_block k points (0: all) times
+ * bands_per_block bands n: for each block the n grids, rho, the weights and
+ * the contraction, whose results are summed into chi0 (Eq. X_IP is a sum
+ * over transitions; only the order of the additions changes).  Device
+ * memory then holds one block's grids and rho instead of all of them.
+ * bands_per_block = 0 switches streaming off.  Takes effect at the next
+ * chi0_compute_rho.  While on, chi0_get_rho / chi0_get_rho_rows return
+ * CHI0_ESTATE and chi0_build_sigma_i CHI0_EUNSUPPORTED; chi0_compute_rho
+ * returns CHI0_EUNSUPPORTED with the extrapolar correction, the learned
+ * terminator or pole grouping set.  Errors: CHI0_EINVAL. */
+chi0_status chi0_set_band_blocks(chi0_ctx* ctx, int bands_per_block, int k_per_block);
+
 /* Wait for all work queued by this context and report device-side errors
  * (CHI0_ETIMEOUT, CHI0_ENOTPD, CHI0_ECUDA).  Reading an error clears the
  * device flag, so the context stays usable. */

@@ -290,6 +290,15 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
                   "fft[%d] = %d aliases: need > 2*%d + %d for these spheres and response set", d,
                   n, L[d], hmax);
   }
+  const bool streamed = c->stream_nb > 0;
+  if (streamed) {
+    if (c->bg_on || c->term_params || c->grp_thresh > 0.0)
+      return fail(c, CHI0_EUNSUPPORTED,
+                  "band-block streaming excludes the extrapolar correction, the learned terminator and pole grouping");
+    c->blk_nb = std::max(1, std::min(c->stream_nb, c->Nn));
+    c->blk_nk = std::max(1, std::min(c->stream_nk > 0 ? c->stream_nk : c->nk, c->nk));
+    c->nt_blk = (int64_t)c->blk_nk * c->blk_nb * c->Nm;
+  }
   c->rho_iq = c->chi_iq = c->eps_iq = -1;
   c->plan_rho_iq = iq;
   if (c->nt == 0) {
@@ -299,9 +308,14 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
   }
   // ---- device buffers
   const size_t cb = cplx_bytes(c);
-  const size_t ubytes = (size_t)c->nk * c->nb * g.N1 * g.NZ * g.N2 * cb;
+  const size_t plane_bytes = (size_t)g.N1 * g.NZ * g.N2 * cb;
+  // streamed: the m-band grids of every k (resident) and one block's n grids
+  const size_t ubytes = streamed ? (size_t)c->nk * c->Nm * plane_bytes : (size_t)c->nk * c->nb * plane_bytes;
   if ((s = ensure(c, c->d_U, ubytes, "mixed-grid wavefunctions")) != CHI0_OK) return s;
-  if ((s = ensure(c, c->d_R, (size_t)c->nt * g.ng * cb, "rho")) != CHI0_OK) return s;
+  if (streamed &&
+      (s = ensure(c, c->d_Ublk, (size_t)c->blk_nk * c->blk_nb * plane_bytes, "mixed grids of a band block")) != CHI0_OK)
+    return s;
+  if ((s = ensure(c, c->d_R, (size_t)(streamed ? c->nt_blk : c->nt) * g.ng * cb, "rho")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_gresp, (size_t)g.ng * 12, "G set")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_gperm, (size_t)g.ng * 4, "G order")) != CHI0_OK) return s;
   if ((s = ensure(c, c->d_kq, (size_t)c->nk * 4, "k pairs")) != CHI0_OK) return s;
@@ -354,27 +368,37 @@ chi0_status plan_rho(chi0_ctx* c, int iq) {
   return CHI0_OK;
 }
 
+// wavefunctions to the mixed grid: every k and band (nkr = 0), or the k
+// points k0 .. k0 + nkr - 1 and bands b0 .. b0 + nbo - 1 into U[k - k0][b - b0]
+cudaError_t launch_wf_range(chi0_ctx* c, void* U, int k0, int nkr, int b0, int nbo) {
+  const RhoGeom& g = c->geom;
+  chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
+  cudaError_t e;
+  if (c->fp64)
+    e = chi0::launch_wf_to_mixed<double>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
+                                         (const double2*)c->d_coef.p, (const double2*)c->d_tw1.p,
+                                         (const double2*)c->d_tw2.p, (double2*)U, c->st, k0, nkr, b0, nbo);
+  else
+    e = chi0::launch_wf_to_mixed<float>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
+                                        (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
+                                        (const float2*)c->d_tw2.p, (float2*)U, c->st, k0, nkr, b0, nbo);
+  if (e == cudaSuccess) chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
+  return e;
+}
+
 // kernels of compute_rho (wavefunctions to the mixed grid; rho unless the
-// caller runs rho for many problems in one batched launch)
+// caller runs rho for many problems in one batched launch, or the
+// transitions are streamed in band blocks by build_chi0)
 chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
   const int iq = c->plan_rho_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "rho not planned");
   if (c->nt > 0 && !c->grid_shared) {
-    const RhoGeom& g = c->geom;
-    cudaError_t e;
-    chi0::stage_begin(c, CHI0_STAGE_WF_GRID);
-    if (c->fp64)
-      e = chi0::launch_wf_to_mixed<double>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
-                                           (const double2*)c->d_coef.p, (const double2*)c->d_tw1.p,
-                                           (const double2*)c->d_tw2.p, (double2*)c->d_U.p, c->st);
-    else
-      e = chi0::launch_wf_to_mixed<float>(g, (const int32_t*)c->d_gvec.p, (const int32_t*)c->d_npw.p,
-                                          (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
-                                          (const float2*)c->d_tw2.p, (float2*)c->d_U.p, c->st);
+    // streamed: the grids of the m bands 0 .. Nm - 1 at every k only
+    const int nkr = c->stream_nb > 0 ? c->nk : 0, nbo = c->stream_nb > 0 ? c->Nm : 0;
+    cudaError_t e = launch_wf_range(c, c->d_U.p, 0, nkr, 0, nbo);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
-    chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
   }
-  if (c->nt > 0) {
+  if (c->nt > 0 && c->stream_nb == 0) {
     const RhoGeom& g = c->geom;
     cudaError_t e;
     if (with_pairs) {
@@ -650,7 +674,9 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
     CK(cudaStreamSynchronize(c->st), "synchronize");
   }
   if (c->nt > 0) {
-    if ((s = ensure(c, c->d_w, (size_t)c->nt * nw * 8, "weights")) != CHI0_OK) return s;
+    // transitions per contraction: all of them, or one band block's
+    const int64_t ntc = c->stream_nb > 0 ? c->nt_blk : c->nt;
+    if ((s = ensure(c, c->d_w, (size_t)ntc * nw * 8, "weights")) != CHI0_OK) return s;
     if ((s = ensure(c, c->d_omim, (size_t)nw * 8, "frequencies")) != CHI0_OK) return s;
     if ((s = ensure(c, c->d_vkind, (size_t)nw * 4, "frequency kinds")) != CHI0_OK) return s;
     CK(cudaMemcpyAsync(c->d_omim.p, c->h_vval.data(), nw * 8, cudaMemcpyHostToDevice, c->st), "omega H2D");
@@ -662,12 +688,12 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
       const int64_t tiles = (int64_t)nT * (nT + 1) / 2 * nw;
       int64_t want = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
       const int64_t mem_cap = std::max<int64_t>(1, (int64_t)(8ull << 30) / (int64_t)(n2 * nw * 16));
-      want = std::min<int64_t>({want, mem_cap, (c->nt + 63) / 64});
+      want = std::min<int64_t>({want, mem_cap, (ntc + 63) / 64});
       c->nchunks = (int)std::max<int64_t>(1, want);
-      c->kchunk = (int)((c->nt + c->nchunks - 1) / c->nchunks);
+      c->kchunk = (int)((ntc + c->nchunks - 1) / c->nchunks);
       if ((s = ensure(c, c->d_part, n2 * nw * c->nchunks * 16, "chi0 partials")) != CHI0_OK) return s;
     } else {
-      if ((s = chi0::tc_plan(c, c->nt, ng, nw)) != CHI0_OK) return s;
+      if ((s = chi0::tc_plan(c, ntc, ng, nw)) != CHI0_OK) return s;
     }
     if (c->term_params && (s = chi0::term_plan(c, iq)) != CHI0_OK) return s;
     if (c->bg_on && (s = plan_bg(c)) != CHI0_OK) return s;
@@ -695,6 +721,82 @@ chi0_status launch_weights_stage(chi0_ctx* c) {
   return CHI0_OK;
 }
 
+// Band-block streaming: for every block of blk_nk k points and blk_nb n
+// bands, the n grids of the block, its rho (m grids from the resident d_U),
+// its weights and its contraction, summed into chi0 (the first block writes,
+// the later ones add).  The blocks partition the transition set of the
+// unstreamed form, so the sum is the same chi0 (Eq. X_IP is a sum over
+// transitions) up to the order of the additions.
+chi0_status launch_chi0_streamed(chi0_ctx* c) {
+  const int nw = c->nwv, ng = c->cfg.ng;
+  const size_t n2 = (size_t)ng * ng;
+  double2* chiv = c->has_real ? (double2*)c->d_chiv.p : (double2*)c->d_chi.p;
+  const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
+  int blk = 0;
+  double bytes = 0.0;
+  for (int k0 = 0; k0 < c->nk; k0 += c->blk_nk) {
+    const int nkb = std::min(c->blk_nk, c->nk - k0);
+    for (int b0 = c->n_lo; b0 < c->nb; b0 += c->blk_nb, ++blk) {
+      const int nbb = std::min(c->blk_nb, c->nb - b0);
+      const int64_t ntb = (int64_t)nkb * nbb * c->Nm;
+      cudaError_t e = launch_wf_range(c, c->d_Ublk.p, k0, nkb, b0, nbb);
+      if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch (band block)");
+      RhoGeom gb = c->geom;
+      gb.nk = nkb;
+      gb.k0 = k0;
+      gb.n_lo = b0;
+      gb.Nn = nbb;
+      gb.nbu = nbb;
+      gb.bu0 = b0;
+      gb.nbm = c->Nm;
+      chi0::stage_begin(c, CHI0_STAGE_RHO);
+      if (c->fp64)
+        e = chi0::launch_rho_pairs<double, double2>(
+            gb, (const double2*)c->d_Ublk.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+            (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const double2*)c->d_tw1.p,
+            (const double2*)c->d_tw2.p, (double2*)c->d_R.p, c->st, (const double2*)c->d_U.p);
+      else
+        e = chi0::launch_rho_pairs<float, float2>(
+            gb, (const float2*)c->d_Ublk.p, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+            (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p,
+            (const float2*)c->d_tw2.p, (float2*)c->d_R.p, c->st, (const float2*)c->d_U.p);
+      if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch (band block)");
+      chi0::stage_end(c, CHI0_STAGE_RHO, 1);
+      chi0::stage_begin(c, CHI0_STAGE_WEIGHTS);
+      e = chi0::launch_weights(nkb, b0, nbb, c->Nm, c->nb, (const int32_t*)c->d_kq.p, (const double*)c->d_eps.p,
+                               (const double*)c->d_occ.p, (const double*)c->d_omim.p, (const int*)c->d_vkind.p, nw,
+                               c->cfg.eta, pref, c->cfg.occ_drop_tol, 0, 0.0, nullptr,
+                               c->dg_nd > 0 ? (const double*)c->d_epsd.p : nullptr, c->dg_nd, (double*)c->d_w.p,
+                               c->st, k0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "weights launch (band block)");
+      chi0::stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+      chi0_status s;
+      if (c->fp64) {
+        chi0::stage_begin(c, CHI0_STAGE_CONTRACT);
+        e = chi0::launch_chi0_fp64_partials((const double2*)c->d_R.p, (const double*)c->d_w.p, ntb, ng, nw,
+                                            c->kchunk, c->nchunks, (double2*)c->d_part.p, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "chi0 fp64 launch (band block)");
+        chi0::stage_end(c, CHI0_STAGE_CONTRACT, 1);
+        chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+        e = chi0::launch_chi0_reduce((const double2*)c->d_part.p, c->nchunks, ng, nw, chiv, c->st, blk > 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "chi0 reduce launch (band block)");
+        chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+      } else {
+        s = chi0::tc_launch(c, c->d_R.p, (const double*)c->d_w.p, ntb, ng, nw, chiv, nullptr, nullptr, nullptr,
+                            c->has_real ? c->h_vkind.data() : nullptr, blk > 0);
+        if (s != CHI0_OK) return s;
+        bytes += c->stage[CHI0_STAGE_CONTRACT].bytes;
+      }
+    }
+  }
+  c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)c->nt * nw;
+  if (!c->fp64) c->stage[CHI0_STAGE_CONTRACT].bytes = bytes;
+  else c->stage[CHI0_STAGE_CONTRACT].bytes = (double)c->nt * ng * 16 + (double)c->nt * nw * 8;
+  c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * nw * 8;
+  (void)n2;
+  return CHI0_OK;
+}
+
 // kernels of build_chi0 (weights, contraction, reduction, terminator)
 chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep, bool defer_combine) {
   const int iq = c->plan_chi_iq;
@@ -704,6 +806,16 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
   chi0_status s;
   if (c->nt == 0) {
     CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw0 * 16, c->st), "zero chi0");
+  } else if (c->stream_nb > 0) {
+    if ((s = launch_chi0_streamed(c)) != CHI0_OK) return s;
+    if (c->has_real && !defer_combine) {
+      double2* chiv = (double2*)c->d_chiv.p;
+      chi0::stage_begin(c, CHI0_STAGE_REDUCE);
+      cudaError_t e = chi0::launch_combine_freq(chiv, (const int*)c->d_vr.p, (const int*)c->d_vi.p, ng, nw0,
+                                                (double2*)c->d_chi.p, c->st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "frequency combine launch");
+      chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
+    }
   } else {
     // the contraction's output: chi0 itself, or its parts H_r, H_i per real frequency
     double2* chiv = c->has_real ? (double2*)c->d_chiv.p : (double2*)c->d_chi.p;
@@ -852,7 +964,7 @@ chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
   if (iq < 0 || c->plan_eps_iq != iq) return fail(c, CHI0_ESTATE, "build and Dyson step not planned");
   const int nw = c->cfg.nw, ng = c->cfg.ng;
   chi0_status s;
-  if (c->fp64 || c->term_params || c->nt == 0 || nw < 2) {
+  if (c->fp64 || c->term_params || c->nt == 0 || nw < 2 || c->stream_nb > 0) {
     // FP64 contraction and Dyson share the FP64 pipe; the learned terminator
     // needs every frequency of chi0 first: no overlap to gain
     if ((s = launch_chi0(c)) != CHI0_OK) return s;
@@ -1245,6 +1357,8 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
   const int nqp = qp_hi - qp_lo;
   if (nqp > 64) return fail(c, CHI0_EUNSUPPORTED, "at most 64 bands in the quasiparticle window");
   if (iq != c->rho_iq) return fail(c, CHI0_ESTATE, "chi0_compute_rho(%d) must come first", iq);
+  if (c->stream_nb > 0)
+    return fail(c, CHI0_EUNSUPPORTED, "the self-energy kernel needs every band's mixed grids (no band-block streaming)");
   if (c->nt == 0)
     return fail(c, CHI0_ESTATE, "no transitions at this q: the mixed-grid wavefunctions were not built");
   const int ng = c->cfg.ng, nb = c->nb;
@@ -1358,6 +1472,18 @@ chi0_status chi0_build_sigma_i(chi0_ctx* c, int iq, int qp_lo, int qp_hi, const 
   return CHI0_OK;
 }
 
+chi0_status chi0_set_band_blocks(chi0_ctx* c, int bands_per_block, int k_per_block) {
+  if (!c) return CHI0_EINVAL;
+  if (bands_per_block < 0 || k_per_block < 0)
+    return fail(c, CHI0_EINVAL, "band and k block sizes must be >= 0");
+  c->stream_nb = bands_per_block;
+  c->stream_nk = bands_per_block > 0 ? k_per_block : 0;
+  ++c->plan_epoch;
+  c->rho_iq = c->chi_iq = c->eps_iq = -1;
+  c->plan_rho_iq = c->plan_chi_iq = c->plan_eps_iq = -1;
+  return CHI0_OK;
+}
+
 chi0_status chi0_set_pole_grouping(chi0_ctx* c, double eps_thresh) {
   if (!c) return CHI0_EINVAL;
   if (!std::isfinite(eps_thresh) || eps_thresh < 0.0)
@@ -1419,6 +1545,7 @@ chi0_status chi0_get_transitions(chi0_ctx* c, int64_t* nt, int32_t* out) {
 chi0_status chi0_get_rho(chi0_ctx* c, void* out) {
   if (!c) return CHI0_EINVAL;
   if (c->rho_iq < 0) return fail(c, CHI0_ESTATE, "no rho before chi0_compute_rho");
+  if (c->stream_nb > 0) return fail(c, CHI0_ESTATE, "rho is not kept when the transitions are streamed in band blocks");
   if (!out) return fail(c, CHI0_EINVAL, "NULL out");
   const size_t n = (size_t)c->nt * c->cfg.ng;
   if (n == 0) return CHI0_OK;
@@ -1438,6 +1565,7 @@ chi0_status chi0_get_rho(chi0_ctx* c, void* out) {
 chi0_status chi0_get_rho_rows(chi0_ctx* c, const int64_t* rows, int64_t nrows, void* out) {
   if (!c) return CHI0_EINVAL;
   if (c->rho_iq < 0) return fail(c, CHI0_ESTATE, "no rho before chi0_compute_rho");
+  if (c->stream_nb > 0) return fail(c, CHI0_ESTATE, "rho is not kept when the transitions are streamed in band blocks");
   if (nrows < 0 || (nrows > 0 && (!rows || !out))) return fail(c, CHI0_EINVAL, "bad rows/out");
   const int ng = c->cfg.ng;
   const size_t cb = cplx_bytes(c);
@@ -1520,7 +1648,7 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
                     &c->d_termq, &c->d_termw, &c->d_termc, &c->d_bgd, &c->d_bgperm, &c->d_bgkq,
                     &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx, &c->d_sigR, &c->d_sigWd,
-                    &c->d_sigY, &c->d_sigI, &c->d_sigRT, &c->d_dpole, &c->d_epsd};
+                    &c->d_sigY, &c->d_sigI, &c->d_sigRT, &c->d_dpole, &c->d_epsd, &c->d_Ublk};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)

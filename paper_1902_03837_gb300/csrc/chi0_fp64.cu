@@ -39,14 +39,14 @@ __global__ void k_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32_
                           const double* __restrict__ omega_im, const int* __restrict__ vkind, int nw,
                           double eta, double pref, double occ_tol, int bg, double eps_bar,
                           const double* __restrict__ dpole, const double* __restrict__ epsd, int nd,
-                          double* __restrict__ w) {
+                          double* __restrict__ w, int k0) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const int m = (int)(t % Nm);
   const int64_t r = t / Nm;
   const int n = n_lo + (int)(r % Nn);
-  const int ik = (int)(r / Nn);
+  const int ik = k0 + (int)(r / Nn);   // global k (the transitions cover k0 .. k0 + nk - 1)
   const int ikp = kq[ik];
   const double df = occ[(size_t)ikp * nb + m] - occ[(size_t)ik * nb + n];
   const double d = eps[(size_t)ikp * nb + m] - eps[(size_t)ik * nb + n];
@@ -153,7 +153,7 @@ k_chi0_fp64(const double2* __restrict__ R, const double* __restrict__ w, int64_t
 
 // chi[iw][i][j] (i >= j) = sum_kc part, then chi[iw][j][i] = conj(chi[iw][i][j]).
 __global__ void k_chi0_reduce(const double2* __restrict__ part, int nchunks, int ng, int nw,
-                              double2* __restrict__ chi) {
+                              double2* __restrict__ chi, int accumulate) {
   const int64_t n2 = (int64_t)ng * ng;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n2 * nw) return;
@@ -169,6 +169,11 @@ __global__ void k_chi0_reduce(const double2* __restrict__ part, int nchunks, int
   }
   double2* o = chi + (size_t)iw * n2;
   if (i == j) sy = 0.0;  // Hermitian: real diagonal
+  if (accumulate) {      // add to the sum of the earlier transition blocks
+    const double2 a = o[(size_t)i * ng + j];
+    sx += a.x;
+    sy += a.y;
+  }
   o[(size_t)i * ng + j] = make_double2(sx, sy);
   if (i != j) o[(size_t)j * ng + i] = make_double2(sx, -sy);
 }
@@ -179,12 +184,12 @@ cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32
                            const double* eps, const double* occ, const double* omega_im,
                            const int* vkind, int nw, double eta, double pref,
                            double occ_tol, int bg, double eps_bar, const double* dpole, const double* epsd,
-                           int nd, double* w, cudaStream_t s) {
+                           int nd, double* w, cudaStream_t s, int k0) {
   const int64_t nt = (int64_t)nk * Nn * Nm;
   if (nt == 0) return cudaSuccess;
   const int64_t blocks = (nt + 255) / 256;
   k_weights<<<(unsigned)blocks, 256, 0, s>>>(nk, n_lo, Nn, Nm, nb, kq, eps, occ, omega_im, vkind, nw, eta,
-                                            pref, occ_tol, bg, eps_bar, dpole, epsd, nd, w);
+                                            pref, occ_tol, bg, eps_bar, dpole, epsd, nd, w, k0);
   return cudaGetLastError();
 }
 
@@ -220,9 +225,9 @@ cudaError_t launch_combine_freq(const double2* H, const int* vr, const int* vi, 
 }
 
 cudaError_t launch_chi0_reduce(const double2* part, int nchunks, int ng, int nw, double2* chi,
-                               cudaStream_t s) {
+                               cudaStream_t s, int accumulate) {
   const int64_t n = (int64_t)ng * ng * nw;
-  k_chi0_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nchunks, ng, nw, chi);
+  k_chi0_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nchunks, ng, nw, chi, accumulate);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,15 @@ struct chi0_ctx {
   // transforms); group_cap > 0 limits the frequencies per operand-split pass
   bool grid_shared = false;
   int group_cap = 0;
+  // band-block streaming (chi0_set_band_blocks): 0 = off.  When on, the mixed
+  // grids of the m bands (occupied side) stay resident for every k (d_U), and
+  // the transitions go through rho, weights and the contraction in blocks of
+  // blk_nk k points x blk_nb n bands (n grids of a block in d_Ublk, its rho in
+  // d_R), chi0 summed over the blocks
+  int stream_nb = 0, stream_nk = 0;
+  int blk_nb = 0, blk_nk = 0;
+  int64_t nt_blk = 0;
+  DevBuf d_Ublk;
   // Plan reuse: a plan stays valid while nothing it was made from changes.
   // plan_epoch advances whenever an input that shapes a plan changes (Miller
   // indices or sphere sizes, energies or occupations, and the settings of the
@@ -138,10 +147,11 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw);
 // vkind (optional, host, [nw]): kinds of the frequency list; an entry of kind 1
 // followed by one of kind 2 is contracted once with the complex weights
 // w[v] + i w[v + 1] over the full tile grid, its chi0 written at entry v
+// accumulate: chi += this contraction (the transitions come in blocks)
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq = nullptr,
                       const cudaEvent_t* ev_prep = nullptr, const chi0::BgApply* bg = nullptr,
-                      const int* vkind = nullptr);
+                      const int* vkind = nullptr, int accumulate = 0);
 void tc_release(chi0_ctx* c);
 // one bounded mbarrier wait that can never be satisfied (failure detection)
 cudaError_t launch_wait_probe(int* err, cudaStream_t s);

@@ -32,6 +32,11 @@ struct RhoGeom {
   int g0z_min, g0z_max;    // range of G0_z over the k-pairs
   int diag;                // 1: the m grid is band n_lo + n at the same k (Nm = 1):
                            // diagonal densities <n k| e^{i G.r} |n k>
+  // Band/k blocks (0 = the whole problem): the transitions cover the k
+  // points k0 .. k0 + nk - 1; the n grids sit in an array of nbu bands per
+  // local k whose first band is bu0; the m grids in an array of nbm bands per
+  // (global) k, separate from the n grids when the task's Um is set.
+  int k0, nbu, bu0, nbm;
 };
 
 // Zero padding of the n plane in the rho kernel's shared memory.
@@ -46,6 +51,7 @@ struct RhoTask {
   RhoGeom g;
   RhoSmem sm;
   const typename C2<T>::t* U;
+  const typename C2<T>::t* Um;  // m grids (NULL: in U)
   const int32_t* kq;
   const int32_t* g0;
   const int32_t* gresp;
@@ -59,21 +65,24 @@ struct RhoTask {
 
 // ---- launchers (stream-ordered; return cudaGetLastError()) ----
 
-// a1: sphere -> mixed grid U[k][band][x][gz][y] for every k and band.
+// a1: sphere -> mixed grid U[k][band][x][gz][y] for every k and band, or
+// (nkr > 0) for the k points k0 .. k0 + nkr - 1 and bands b0 .. b0 + nbo - 1
+// only, written as U[k - k0][band - b0] (coefficients indexed globally).
 template <typename T>
 cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int32_t* npw,
                                const typename C2<T>::t* coef, const typename C2<T>::t* tw1,
                                const typename C2<T>::t* tw2, typename C2<T>::t* U,
-                               cudaStream_t s);
+                               cudaStream_t s, int k0 = 0, int nkr = 0, int b0 = 0, int nbo = 0);
 
 // a2: rho for every transition of the dense (k, n, m) block, written to
 // R[t][i], t = ((ik * Nn) + (n - n_lo)) * Nm + m.  gperm: the response indices
 // ordered by (Gy, Gz, Gx) (the order in which a block's threads visit them).
+// Um (optional): the m grids in an array of their own (see RhoGeom::nbm).
 template <typename T, typename TOUT>
 cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
                              const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
                              const typename C2<T>::t* tw1, const typename C2<T>::t* tw2,
-                             TOUT* R, cudaStream_t s);
+                             TOUT* R, cudaStream_t s, const typename C2<T>::t* Um = nullptr);
 
 // Fill a task for the rho kernels with at most jm_max m bands per block;
 // *smem = its shared memory with a JM = jm_max kernel, *nblocks its blocks.
@@ -106,7 +115,7 @@ cudaError_t launch_weights(int nk, int n_lo, int Nn, int Nm, int nb, const int32
                            const double* eps, const double* occ, const double* omega_im,
                            const int* vkind, int nw, double eta, double pref,
                            double occ_tol, int bg, double eps_bar, const double* dpole, const double* epsd,
-                           int nd, double* w, cudaStream_t s);
+                           int nd, double* w, cudaStream_t s, int k0 = 0);
 // chi[iw] = H[vr[iw]] + i H[vi[iw]] (vi[iw] < 0: chi[iw] = H[vr[iw]])
 cudaError_t launch_combine_freq(const double2* H, const int* vr, const int* vi, int ng, int nw, double2* chi,
                                 cudaStream_t s);
@@ -140,9 +149,10 @@ struct BgApply {
 cudaError_t launch_chi0_fp64_partials(const double2* R, const double* w, int64_t nt, int ng,
                                       int nw, int kchunk, int nchunks, double2* part,
                                       cudaStream_t s);
-// Sum of the partials, Hermitian completion: chi[iw][i][j].
+// Sum of the partials, Hermitian completion: chi[iw][i][j] (accumulate: added
+// to what chi holds, the sum over earlier transition blocks).
 cudaError_t launch_chi0_reduce(const double2* part, int nchunks, int ng, int nw, double2* chi,
-                               cudaStream_t s);
+                               cudaStream_t s, int accumulate = 0);
 
 // a5: eps~ = 1 - V chi V, then in-place blocked Gauss-Jordan inverse.
 cudaError_t launch_dyson(const double2* chi, const double* vsqrt, int ng, int nw, double2* A,

@@ -115,14 +115,17 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_wf_to_mixed(RhoGeom g, const int32_t* __restrict__ gvec, const int32_t* __restrict__ npw,
               const typename C2<T>::t* __restrict__ coef, const typename C2<T>::t* __restrict__ tw1,
-              const typename C2<T>::t* __restrict__ tw2, typename C2<T>::t* __restrict__ U) {
+              const typename C2<T>::t* __restrict__ tw2, typename C2<T>::t* __restrict__ U, int k0,
+              int b0, int nbo) {
   using T2 = typename C2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* box = reinterpret_cast<T2*>(smem_raw);  // [NZ][NX][NY]
   T2* t1 = box + g.NZ * g.NX * g.NY;          // [NX][N2]
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int ik = blockIdx.x / g.nb;
-  const int band = blockIdx.x - ik * g.nb;
+  const int ikl = blockIdx.x / nbo;           // local k and band of the output
+  const int bl = blockIdx.x - ikl * nbo;
+  const int ik = k0 + ikl;                    // global k and band of the coefficients
+  const int band = b0 + bl;
   const int nbox = g.NZ * g.NX * g.NY;
   for (int i = tid; i < nbox; i += nth) box[i] = czero<T2>();
   __syncthreads();
@@ -134,7 +137,7 @@ k_wf_to_mixed(RhoGeom g, const int32_t* __restrict__ gvec, const int32_t* __rest
     box[((gz + g.Lz) * g.NX + (gx + g.Lx)) * g.NY + (gy + g.Ly)] = c[p];
   }
   __syncthreads();
-  T2* out = U + ((size_t)ik * g.nb + band) * ((size_t)g.N1 * g.NZ * g.N2);
+  T2* out = U + ((size_t)ikl * nbo + bl) * ((size_t)g.N1 * g.NZ * g.N2);
   if (g.N1 % 4 == 0 && g.N2 % 4 == 0) {
     // Radix-4 on the output side: with N = 4 Q and x = x0 + Q x1,
     //   u(x0 + Q x1) = sum_c i^{c x1} S_c(x0),  S_c(x0) = sum_{g = c mod 4} a(g) e^{2 pi i g x0 / N},
@@ -296,8 +299,9 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
   const int ik = (int)(blk / ((int64_t)nmc * g.Nn));
   const int m0 = mc * jm;
   const int cm = min(jm, g.Nm - m0);
-  const int ikp = kq[ik];
-  const int G0x = g0[3 * ik], G0y = g0[3 * ik + 1], G0z = g0[3 * ik + 2];
+  const int ikg = g.k0 + ik;  // global k of the transition (ik is local to the block)
+  const int ikp = kq[ikg];
+  const int G0x = g0[3 * ikg], G0y = g0[3 * ikg + 1], G0z = g0[3 * ikg + 2];
   const int NZ = g.NZ, N2 = g.N2, HZ = g.HZ, HY = g.HY;
   const int N2P = N2 + 1;  // padded row of zs: column reads in stage Y hit distinct banks
   const size_t plane = (size_t)NZ * N2;
@@ -349,8 +353,10 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
     }
   }
 
-  const T2* Un = U + ((size_t)ik * g.nb + (g.n_lo + nrel)) * ((size_t)g.N1 * plane);
-  const T2* Um = U + ((size_t)ikp * g.nb + m0 + (g.diag ? g.n_lo + nrel : 0)) * ((size_t)g.N1 * plane);
+  const int nbu = g.nbu ? g.nbu : g.nb, nbm = g.nbm ? g.nbm : g.nb;
+  const T2* Un = U + ((size_t)ik * nbu + (g.n_lo - g.bu0 + nrel)) * ((size_t)g.N1 * plane);
+  const T2* Um = (tk.Um ? tk.Um : U) +
+                 ((size_t)ikp * nbm + m0 + (g.diag ? g.n_lo + nrel : 0)) * ((size_t)g.N1 * plane);
   const size_t band_stride = (size_t)g.N1 * plane;
   const int nhb = (HZ + kHZT - 1) / kHZT;
   const int nyb = (HY + kHYT - 1) / kHYT;
@@ -677,14 +683,21 @@ template <typename T>
 cudaError_t launch_wf_to_mixed(const RhoGeom& g, const int32_t* gvec, const int32_t* npw,
                                const typename C2<T>::t* coef, const typename C2<T>::t* tw1,
                                const typename C2<T>::t* tw2, typename C2<T>::t* U,
-                               cudaStream_t s) {
+                               cudaStream_t s, int k0, int nkr, int b0, int nbo) {
   using T2 = typename C2<T>::t;
   const size_t smem = ((size_t)g.NZ * g.NX * g.NY + (size_t)g.NX * g.N2) * sizeof(T2);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (nkr <= 0) {  // every k and band
+    k0 = 0;
+    nkr = g.nk;
+    b0 = 0;
+    nbo = g.nb;
+  }
+  if (k0 < 0 || b0 < 0 || nbo <= 0 || k0 + nkr > g.nk || b0 + nbo > g.nb) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_wf_to_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_wf_to_mixed<T><<<g.nk * g.nb, 256, smem, s>>>(g, gvec, npw, coef, tw1, tw2, U);
+  k_wf_to_mixed<T><<<nkr * nbo, 256, smem, s>>>(g, gvec, npw, coef, tw1, tw2, U, k0, b0, nbo);
   return cudaGetLastError();
 }
 
@@ -721,6 +734,7 @@ cudaError_t rho_task_make(const RhoGeom& g, const typename C2<T>::t* U, const in
   tk->g = g;
   tk->sm = sm;
   tk->U = U;
+  tk->Um = nullptr;
   tk->kq = kq;
   tk->g0 = g0;
   tk->gresp = gresp;
@@ -738,7 +752,7 @@ template <typename T, typename TOUT>
 cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const int32_t* kq,
                              const int32_t* g0, const int32_t* gresp, const int32_t* gperm,
                              const typename C2<T>::t* tw1, const typename C2<T>::t* tw2, TOUT* R,
-                             cudaStream_t s) {
+                             cudaStream_t s, const typename C2<T>::t* Um) {
   if (g.Nn <= 0 || g.Nm <= 0 || g.nk <= 0) return cudaSuccess;
   for (int jm : {4, 2, 1}) {
     RhoTask<T, TOUT> tk;
@@ -746,6 +760,7 @@ cudaError_t launch_rho_pairs(const RhoGeom& g, const typename C2<T>::t* U, const
     int64_t nb = 0;
     cudaError_t e = rho_task_make<T, TOUT>(g, U, kq, g0, gresp, gperm, tw1, tw2, R, jm, &tk, &smem, &nb);
     if (e != cudaSuccess) return e;
+    tk.Um = Um;
     if (tk.jm != jm || smem > 227 * 1024) continue;
     switch (jm) {
       case 4: return launch_rho_jm<T, 4, TOUT>(tk, smem, nb, s);
@@ -786,10 +801,10 @@ cudaError_t launch_rho_batch(const RhoTask<T, TOUT>* tasks_dev, int ntasks, int6
 
 template cudaError_t launch_wf_to_mixed<double>(const RhoGeom&, const int32_t*, const int32_t*,
                                                 const double2*, const double2*, const double2*,
-                                                double2*, cudaStream_t);
+                                                double2*, cudaStream_t, int, int, int, int);
 template cudaError_t launch_wf_to_mixed<float>(const RhoGeom&, const int32_t*, const int32_t*,
                                                const float2*, const float2*, const float2*,
-                                               float2*, cudaStream_t);
+                                               float2*, cudaStream_t, int, int, int, int);
 template cudaError_t rho_task_make<double, double2>(const RhoGeom&, const double2*, const int32_t*,
                                                     const int32_t*, const int32_t*, const int32_t*,
                                                     const double2*, const double2*, double2*, int,
@@ -806,10 +821,10 @@ template cudaError_t launch_rho_pairs<double, double2>(const RhoGeom&, const dou
                                                        const int32_t*, const int32_t*,
                                                        const int32_t*, const int32_t*,
                                                        const double2*, const double2*, double2*,
-                                                       cudaStream_t);
+                                                       cudaStream_t, const double2*);
 template cudaError_t launch_rho_pairs<float, float2>(const RhoGeom&, const float2*, const int32_t*,
                                                      const int32_t*, const int32_t*, const int32_t*,
                                                      const float2*, const float2*, float2*,
-                                                     cudaStream_t);
+                                                     cudaStream_t, const float2*);
 
 }  // namespace chi0

@@ -497,7 +497,7 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
 
 // chi[i][j] (i >= j) = sum over chunks of the partials (FP64), mirrored.
 __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int ntiles, int ng,
-                            double2* __restrict__ chi) {
+                            double2* __restrict__ chi, int accumulate) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
   const int i = (int)(e / ng), j = (int)(e % ng);
@@ -512,6 +512,11 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
     sy += v.y;
   }
   if (i == j) sy = 0.0;  // Hermitian: real diagonal
+  if (accumulate) {      // add to the sum of the earlier transition blocks
+    const double2 a = chi[(size_t)i * ng + j];
+    sx += a.x;
+    sy += a.y;
+  }
   chi[(size_t)i * ng + j] = make_double2(sx, sy);
   if (i != j) chi[(size_t)j * ng + i] = make_double2(sx, -sy);
 }
@@ -519,7 +524,7 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
 // chi[i][j] = sum over chunks of the partials of the full tile grid (A rows i,
 // B rows j: tile (i / 64) + (j / 64) nT), every entry (no Hermitian symmetry).
 __global__ void k_tc_reduce_full(const double2* __restrict__ part, int nchunks, int ntiles, int nT, int ng,
-                                 double2* __restrict__ chi) {
+                                 double2* __restrict__ chi, int accumulate) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
   const int i = (int)(e / ng), j = (int)(e % ng);
@@ -530,6 +535,10 @@ __global__ void k_tc_reduce_full(const double2* __restrict__ part, int nchunks, 
     const double2 v = part[((size_t)c * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
     sx += v.x;
     sy += v.y;
+  }
+  if (accumulate) {
+    sx += chi[e].x;
+    sy += chi[e].y;
   }
   chi[e] = make_double2(sx, sy);
 }
@@ -671,7 +680,7 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
 
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep,
-                      const BgApply* bg, const int* vkind) {
+                      const BgApply* bg, const int* vkind, int accumulate) {
   if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "tensor-core contraction not planned");
   TcState& t = *static_cast<TcState*>(c->tc);
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
@@ -740,10 +749,10 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       stage_begin(c, CHI0_STAGE_REDUCE);
       if (jb.cplx)
         k_tc_reduce_full<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks_f,
-                                                                           t.ntiles_f, nT, ng, out);
+                                                                           t.ntiles_f, nT, ng, out, accumulate);
       else
         k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks, t.ntiles,
-                                                                      ng, out);
+                                                                      ng, out, accumulate);
       int nk = 1;
       if (bg) {
         launch_bg_apply(bg->P + (size_t)jb.v * bg->nd, bg->didx, ng, bg->nd, 1, out, c->st, 0);

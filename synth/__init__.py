@@ -17,6 +17,9 @@ from .systems import (  # noqa: F401
     make_plane_wave_system,
     truncate_bands,
     cfg_learned,
+    cfg_large,
+    large_energies,
+    tr_partner,
     cfg_plain_fp64,
     cfg_precision,
     cfg_tiny,

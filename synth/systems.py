@@ -125,6 +125,11 @@ def gauss_legendre_freqs(n: int, lo_ev: float, hi_ev: float) -> np.ndarray:
     return 1j * (w_ev / HA_EV)
 
 
+def tr_partner(ik: int, kgrid) -> int:
+    """Index of the grid point of -k."""
+    return _tr_partner(ik, kgrid)
+
+
 def _tr_partner(ik: int, kgrid) -> int:
     n1, n2, n3 = kgrid
     i, rem = divmod(ik, n2 * n3)
@@ -270,6 +275,42 @@ def cfg_precision(seed: int = 2, nw: int = 32) -> SystemSpec:
                       fft=(48, 48, 48), ng=1000, q_frac=((0.25, 0.0, 0.0),),
                       freqs=tuple(gauss_legendre_freqs(nw, 0.0, 100.0)), eta=0.0,
                       seed=seed, coef_dtype="c64")
+
+
+def cfg_large(seed: int = 6, kgrid=(12, 12, 12), nw: int = 64) -> SystemSpec:
+    """Large case: 12x12x12 k, 24 occupied + 976 empty bands, ~4000 PW,
+    FFT 72^3, N_G = 3000, 64 imaginary frequencies on a Gauss-Legendre grid
+    in [0, 100] eV, the 8 q points (j/12, 0, 0), j = 1..8, complex64
+    coefficients.  Its states are too many for the host-side generator of
+    this module (1728 QR factorisations of 4000 x 1000): the benchmark
+    generates them on the device by the same recipe; its energies come from
+    large_energies."""
+    q = tuple((j / float(kgrid[0]), 0.0, 0.0) for j in range(1, 9))
+    return SystemSpec(a=10.0, kgrid=tuple(kgrid), n_occ=24, n_bands=1000, kc=6.1842,
+                      fft=(72, 72, 72), ng=3000, q_frac=q,
+                      freqs=tuple(gauss_legendre_freqs(nw, 0.0, 100.0)), eta=0.0,
+                      seed=seed, coef_dtype="c64")
+
+
+def large_energies(spec: SystemSpec) -> np.ndarray:
+    """Band energies of every k (Ha) by the recipe of make_system: per TR pair
+    one draw keyed by (seed, k), occupied ~ U[occ_ev] and empty ~ U[emp_ev],
+    each sorted, shared by the pair."""
+    kgrid = tuple(int(v) for v in spec.kgrid)
+    nk = kgrid[0] * kgrid[1] * kgrid[2]
+    nb = spec.n_bands
+    eps = np.zeros((nk, nb))
+    done = np.zeros(nk, dtype=bool)
+    for ik in range(nk):
+        if done[ik]:
+            continue
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([spec.seed, ik])))
+        e_occ = np.sort(rng.uniform(spec.occ_ev[0], spec.occ_ev[1], spec.n_occ))
+        e_emp = np.sort(rng.uniform(spec.emp_ev[0], spec.emp_ev[1], nb - spec.n_occ))
+        jk = _tr_partner(ik, kgrid)
+        eps[ik] = eps[jk] = np.concatenate([e_occ, e_emp]) / HA_EV
+        done[ik] = done[jk] = True
+    return eps
 
 
 def cfg_tiny(seed: int = 11, kgrid=(2, 2, 2), n_occ=3, n_bands=6, kc=None,
