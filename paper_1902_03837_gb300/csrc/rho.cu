@@ -417,30 +417,38 @@ __device__ __forceinline__ void rho_block(const RhoTask<T, TOUT>& tk, int64_t bl
       const T2* pm = ums + y;
       if (cm == JM) {
         // U_n rows hz .. hz + kHZT - 1 at b slide by one row per b: keep the
-        // window in registers, row b + h of the tile in slot (b + h) % kHZT,
-        // with the b loop unrolled by kHZT so that every slot index is a
-        // constant; one new row is loaded per b, into the slot of the row
-        // that just left the window
-        ZRow<T2> w[kHZT];
+        // window in registers (three names, rotated by unrolling) and load
+        // one new row per b
+        static_assert(kHZT == 3, "the rotation below is written for three rows");
+        ZRow<T2> w0 = zrow(pn[0]), w1 = zrow(pn[N2]), w2;
+        const T2* pl = pn + 2 * N2;  // next row of U_n to load
+        int b = 0;
+        auto step = [&](const ZRow<T2>& r0, const ZRow<T2>& r1, const ZRow<T2>& r2) {
 #pragma unroll
-        for (int h = 0; h < kHZT - 1; ++h) w[h] = zrow(pn[h * N2]);
-        const T2* pl = pn + (kHZT - 1) * N2;  // row b + kHZT - 1 at r = 0
-        for (int b = 0; b < NZ; b += kHZT) {
-#pragma unroll
-          for (int r = 0; r < kHZT; ++r) {
-            if (b + r < NZ) {
-              w[(r + kHZT - 1) % kHZT] = zrow(pl[r * N2]);
-#pragma unroll
-              for (int j = 0; j < JM; ++j) {
-                const T2 um = pm[j * (int)plane];
-                const T2 rm = zrot(um);
-#pragma unroll
-                for (int h = 0; h < kHZT; ++h) zmac(a[j][h], w[(r + h) % kHZT], um, rm);
-              }
-              pm += N2;
-            }
+          for (int j = 0; j < JM; ++j) {
+            const T2 um = pm[j * (int)plane];
+            const T2 rm = zrot(um);
+            zmac(a[j][0], r0, um, rm);
+            zmac(a[j][1], r1, um, rm);
+            zmac(a[j][2], r2, um, rm);
           }
-          pl += kHZT * N2;
+          pm += N2;
+        };
+        for (; b + 3 <= NZ; b += 3) {
+          w2 = zrow(pl[0]);
+          step(w0, w1, w2);
+          w0 = zrow(pl[N2]);
+          step(w1, w2, w0);
+          w1 = zrow(pl[2 * N2]);
+          step(w2, w0, w1);
+          pl += 3 * N2;
+        }
+        for (; b < NZ; ++b) {
+          w2 = zrow(pl[0]);
+          step(w0, w1, w2);
+          w0 = w1;
+          w1 = w2;
+          pl += N2;
         }
       } else {
         for (int b = 0; b < NZ; ++b, pn += N2, pm += N2) {

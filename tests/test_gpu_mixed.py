@@ -147,3 +147,19 @@ def test_precision_workload_full_size(lib):
         for b in parts:
             e_ab = _rel(got[:, a][:, :, b], ref[:, a][:, :, b])
             assert e_ab < TOL, (a[0], b[0], e_ab)
+    # the plain FP64 form (the denominator of the mixed form's speed-up) at
+    # full size, on the first two frequencies, against the same oracle values
+    import dataclasses
+    s2 = dataclasses.replace(s, freqs=s.freqs[:2])
+    ctx = lib.Chi0.for_system(s2, precision=lib.CHI0_FP64, stream=torch.cuda.current_stream().cuda_stream)
+    ctx.load_system(s2)
+    ctx.compute_rho(0)
+    chi64 = torch.zeros((2, ng, ng), dtype=torch.complex128, device="cuda")
+    ctx.build_chi0(0, chi64)
+    ctx.synchronize()
+    ctx.close()
+    got64 = chi64[:, idx][:, :, idx].cpu().numpy()
+    e64 = _rel(got64, ref[:2])
+    print(f"precision workload, plain FP64 form, 96 x 96 G subset, 2 frequencies: {e64:.3e}")
+    assert e64 < 1e-10, e64
+    assert (chi64 - chi64.conj().transpose(1, 2)).abs().max().item() <= 1e-13 * chi64.abs().max().item()
