@@ -176,7 +176,7 @@ def ppa_real_freqs(n):
     return np.arange(1, n + 1) * (100.0 / n) / HA_EV + 0j
 
 
-def build_system(kgrid=None, nw=32, real_axis=False, ppa=False):
+def build_system(kgrid=None, nw=32, real_axis=False, ppa=False, flat=False):
     """The precision workload; kgrid / nw override it for smaller profiling
     runs; real_axis puts its nw frequencies on the real axis instead (evenly
     spaced on (0, 100] eV, broadening 0.1 eV); ppa keeps only the plasmon-pole
@@ -191,6 +191,8 @@ def build_system(kgrid=None, nw=32, real_axis=False, ppa=False):
         spec = dataclasses.replace(spec, freqs=tuple(complex(x, 0.0) for x in w), eta=0.1 / HA_EV)
     if ppa:
         spec = dataclasses.replace(spec, freqs=(0j, 1j * PPA_OMEGA_P))
+    if flat:
+        spec = dataclasses.replace(spec, flat_bands=True)
     return make_system(spec)
 
 
@@ -204,6 +206,10 @@ def workload_name(args):
                             f"model on {args.ppa} real frequencies on (0,100] eV, eta 0.1 eV")
     if getattr(args, "bg_terminator", None) is not None:
         base += f", Bruneval-Gonze extrapolar correction at {args.bg_terminator:g} eV"
+    if getattr(args, "flat_bands", False):
+        base += ", dispersionless bands (every k has the energies of k = 0)"
+    if getattr(args, "grouping", 0.0):
+        base += f", pole grouping at {args.grouping:g} Ha"
     return base
 
 
@@ -419,13 +425,13 @@ def run_reference(args, rank, world):
 
 def run_ours(args, rank, world, dist):
     import torch
-    s = build_system(args.kgrid, args.nw, args.real_axis, ppa=bool(args.ppa))
+    s = build_system(args.kgrid, args.nw, args.real_axis, ppa=bool(args.ppa), flat=args.flat_bands)
     ng, nw = s.ng, s.freqs.size
     # the plain FP64 form and the CPU baseline on the G_0..G_63 sub-block (with
     # the error against it) are measured on the imaginary-axis workload (rank
     # 0 only); the baseline's workers start here, before any CUDA call
     plain = (rank == 0 and args.precision == "mixed" and not args.ppa and not args.real_axis
-             and args.bg_terminator is None)
+             and args.bg_terminator is None and not args.grouping and not args.flat_bands)
     compare = plain and not args.no_compare
     jobs = OracleJobs(s) if (plain and not args.no_cpu_baseline) else None
     import __graft_entry__ as g
@@ -447,6 +453,8 @@ def run_ours(args, rank, world, dist):
     if args.bg_terminator is not None:
         from synth import HA_EV
         ctx.set_bg_terminator(args.bg_terminator / HA_EV)
+    if args.grouping:
+        ctx.set_pole_grouping(args.grouping)
     inv_d = torch.empty((nw, ng, ng), dtype=torch.complex128, device=dev)
     ppa_ms = [0.0, 0.0]
     ppa_launches = 0
@@ -484,6 +492,7 @@ def run_ours(args, rank, world, dist):
         step()
     ctx.synchronize()
     nt = ctx.get_transitions().shape[0]
+    groups = ctx.pole_groups() if args.grouping else None
     ctx.get_stats()  # reset the stage timers
     _, _, _, l0 = ctx.get_stats()
 
@@ -695,6 +704,9 @@ def run_ours(args, rank, world, dist):
     }
     if ppa_line is not None:
         line["ppa"] = ppa_line
+    if groups is not None:
+        line["pole_groups"] = {"threshold_ha": args.grouping, "groups": groups[0],
+                               "grouped_contraction": groups[1]}
     if sigma_line is not None:
         sg = sigma_line
         sg["contract_issued_frac"] = sg["contract_issued_tflops"] / pk["bf16_tflops_sustained"]
@@ -1245,6 +1257,10 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=16, help="systems of the batching workload (from the first)")
     ap.add_argument("--batch-nq", type=int, default=None, help="keep only the first NQ q points of each system")
     ap.add_argument("--batch-streams", type=int, default=4, help="helper streams of the batch")
+    ap.add_argument("--flat-bands", action="store_true",
+                    help="dispersionless bands: every k has the band energies of k = 0 (degenerate poles)")
+    ap.add_argument("--grouping", type=float, default=0.0, metavar="HA",
+                    help="degenerate-pole grouping threshold (Ha); large groups use the grouped contraction")
     ap.add_argument("--terminator", action="store_true",
                     help="the learned-terminator workload: train on chi0 pairs, report the held-out error")
     ap.add_argument("--term-train", type=int, default=200, help="training systems of the terminator workload")

@@ -413,6 +413,22 @@ chi0_status chi0_set_bg_terminator(chi0_ctx* ctx, int on, double eps_bar);
  * [0, 4096]; NULL or non-finite energies; both options set), CHI0_ENOMEM,
  * CHI0_ECUDA. */
 chi0_status chi0_set_pole_grouping(chi0_ctx* ctx, double eps_thresh);
+
+/* The grouping of the last planned chi0 (chi0_build_chi0 / chi0_build_invert
+ * plan it): *ngroups receives the number of pole groups (0 with grouping
+ * off), *grouped_contraction 1 when the groups were large enough for the
+ * grouped contraction.  In the mixed form on the imaginary axis, with neither
+ * correction nor band-block streaming, and when the groups average at least
+ * 32 transitions (padding to 64 at most doubles them) and their sums fit in
+ * 30% of the free device memory, chi0 is built as Appendix B writes it: one
+ * contraction over the transitions in group order gives every group's
+ * frequency-independent sum M_g = sum_{t in g} f_s/(N_k Omega)
+ * (f_m - f_n) rho_t rho_t^H, and each frequency is then
+ * chi0(w) = sum_g F(w, d_g) M_g with the representative's factor, so the
+ * tensor-core work no longer grows with the number of frequencies.  Either
+ * way chi0 is the same sum.  Errors: CHI0_EINVAL, CHI0_ESTATE (nothing
+ * planned). */
+chi0_status chi0_get_pole_groups(chi0_ctx* ctx, int64_t* ngroups, int* grouped_contraction);
 chi0_status chi0_set_double_grid(chi0_ctx* ctx, int nd, const double* eps_dense);
 
 /* ---- Self-energy kernel I (full-frequency GW) --------------------------------

@@ -32,7 +32,7 @@ EXPORTS = (
     "chi0_batch_create", "chi0_batch_run", "chi0_batch_rho_width", "chi0_batch_destroy",
     "chi0_batch_synchronize", "chi0_batch_info",
     "chi0_ppa_fit", "chi0_ppa_eval", "chi0_build_sigma_i", "chi0_set_pole_grouping", "chi0_set_double_grid",
-    "chi0_check_bounded_wait", "chi0_set_band_blocks",
+    "chi0_check_bounded_wait", "chi0_set_band_blocks", "chi0_get_pole_groups",
 )
 
 
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.chi0_set_double_grid.argtypes = [P, I, P]
     lib.chi0_check_bounded_wait.argtypes = [P]
     lib.chi0_set_band_blocks.argtypes = [P, I, I]
+    lib.chi0_get_pole_groups.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I)]
     lib.chi0_ppa_eval.argtypes = [P, P, I, P, I, D, P, P]
     for name in EXPORTS:
         if name not in ("chi0_last_error", "chi0_destroy", "chi0_batch_destroy"):
@@ -376,6 +377,13 @@ class Chi0:
         """chi0_set_band_blocks: stream the transitions in blocks of k_per_block
         k points (0: all) x bands_per_block bands n; 0 bands = off."""
         self._check(_lib.chi0_set_band_blocks(self.h, int(bands_per_block), int(k_per_block)))
+
+    def pole_groups(self):
+        """chi0_get_pole_groups: (number of pole groups, grouped contraction used)."""
+        n = ctypes.c_int64()
+        g = ctypes.c_int()
+        self._check(_lib.chi0_get_pole_groups(self.h, ctypes.byref(n), ctypes.byref(g)))
+        return n.value, bool(g.value)
 
     def set_pole_grouping(self, eps_thresh):
         """chi0_set_pole_grouping: poles within eps_thresh (Ha) share one frequency factor; 0 = off."""

@@ -659,8 +659,10 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
     }
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return d[a] < d[b]; });
     std::vector<double> dp(d);   // transitions without weight keep their own energy
+    std::vector<size_t> gstart;  // first position in `order` of every group
     for (size_t i = 0; i < order.size();) {
       const double dr = d[order[i]];
+      gstart.push_back(i);
       size_t j = i;
       do {
         dp[order[j]] = dr;
@@ -672,6 +674,61 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
     if (s0 != CHI0_OK) return s0;
     CK(cudaMemcpyAsync(c->d_dpole.p, dp.data(), (size_t)nt * 8, cudaMemcpyHostToDevice, c->st), "poles H2D");
     CK(cudaStreamSynchronize(c->st), "synchronize");
+    // The grouped contraction (Appendix B, Eqs. X_IP_split1/2: a factor per
+    // group times the frequency-independent sum of its rho rho^* terms) pays
+    // when the groups are large: one contraction over all transitions gives
+    // the group sums, and each frequency is then a sum over the groups.
+    c->ngroups = (int)std::min<size_t>(gstart.size(), 0x7fffffff);
+    gstart.push_back(order.size());
+    int64_t kgrp = 0;
+    for (int g = 0; g < c->ngroups; ++g) kgrp += (int64_t)((gstart[g + 1] - gstart[g] + 63) / 64) * 64;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    const int nTt = (2 * ng + 127) / 128;
+    const double part_bytes = (double)c->ngroups * (nTt * (nTt + 1) / 2) * 65536.0;
+    c->grouped = !c->fp64 && !c->has_real && !c->bg_on && !c->term_params && c->stream_nb == 0 &&
+                 c->ngroups > 0 && (int64_t)c->ngroups * 32 <= nt && kgrp <= 2 * nt &&
+                 part_bytes <= 0.3 * (double)free_b;
+    if (c->grouped) {
+      c->kgrp = kgrp;
+      std::vector<int64_t> perm((size_t)kgrp, -1);
+      std::vector<int2> ranges(c->ngroups);
+      std::vector<double> ga((size_t)nt, 0.0);
+      std::vector<float> fac((size_t)c->nwv * c->ngroups);
+      const double pref = c->cfg.spin_factor / ((double)c->nk * c->omega_cell);
+      int64_t row = 0;
+      for (int g = 0; g < c->ngroups; ++g) {
+        ranges[g] = make_int2((int)(row / 64), (int)((gstart[g + 1] - gstart[g] + 63) / 64));
+        for (size_t p = gstart[g]; p < gstart[g + 1]; ++p) perm[(size_t)row + (p - gstart[g])] = order[p];
+        row += (int64_t)ranges[g].y * 64;
+        const double drep = d[order[gstart[g]]];
+        for (int v = 0; v < c->nwv; ++v)
+          fac[(size_t)v * c->ngroups + g] = (float)pole_weight_host(0, c->h_vval[v], c->cfg.eta, drep);
+      }
+      for (int64_t t = 0; t < nt; ++t) {
+        const int m = (int)(t % c->Nm);
+        const int64_t r = t / c->Nm;
+        const int n = c->n_lo + (int)(r % c->Nn);
+        const int ik = (int)(r / c->Nn), ikp = c->h_kq[ik];
+        ga[t] = pref * (c->h_occ[(size_t)ikp * nb + m] - c->h_occ[(size_t)ik * nb + n]);
+      }
+      if ((s0 = ensure(c, c->d_tperm, (size_t)kgrp * 8, "group order")) != CHI0_OK) return s0;
+      if ((s0 = ensure(c, c->d_grange, (size_t)c->ngroups * 8, "group ranges")) != CHI0_OK) return s0;
+      if ((s0 = ensure(c, c->d_ga, (size_t)nt * 8, "group weights")) != CHI0_OK) return s0;
+      if ((s0 = ensure(c, c->d_gfac, fac.size() * 4, "group factors")) != CHI0_OK) return s0;
+      CK(cudaMemcpyAsync(c->d_tperm.p, perm.data(), perm.size() * 8, cudaMemcpyHostToDevice, c->st), "order H2D");
+      CK(cudaMemcpyAsync(c->d_grange.p, ranges.data(), ranges.size() * 8, cudaMemcpyHostToDevice, c->st),
+         "ranges H2D");
+      CK(cudaMemcpyAsync(c->d_ga.p, ga.data(), ga.size() * 8, cudaMemcpyHostToDevice, c->st), "weights H2D");
+      CK(cudaMemcpyAsync(c->d_gfac.p, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice, c->st), "factors H2D");
+      CK(cudaStreamSynchronize(c->st), "synchronize");
+    }
+  } else {
+    c->grouped = false;
+    c->ngroups = 0;
   }
   if (c->nt > 0) {
     // transitions per contraction: all of them, or one band block's
@@ -692,6 +749,8 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
       c->nchunks = (int)std::max<int64_t>(1, want);
       c->kchunk = (int)((ntc + c->nchunks - 1) / c->nchunks);
       if ((s = ensure(c, c->d_part, n2 * nw * c->nchunks * 16, "chi0 partials")) != CHI0_OK) return s;
+    } else if (c->grouped) {
+      if ((s = chi0::tc_plan_grouped(c, ng, nw)) != CHI0_OK) return s;
     } else {
       if ((s = chi0::tc_plan(c, ntc, ng, nw)) != CHI0_OK) return s;
     }
@@ -806,6 +865,10 @@ chi0_status launch_chi0(chi0_ctx* c, const cudaEvent_t* ev_freq, const cudaEvent
   chi0_status s;
   if (c->nt == 0) {
     CK(cudaMemsetAsync(c->d_chi.p, 0, n2 * nw0 * 16, c->st), "zero chi0");
+  } else if (c->grouped) {
+    if ((s = chi0::tc_launch_grouped(c, (double2*)c->d_chi.p, ev_freq)) != CHI0_OK) return s;
+    if (ev_prep)
+      for (int v = 0; v < nw; ++v) cudaEventRecord(ev_prep[v], c->st);
   } else if (c->stream_nb > 0) {
     if ((s = launch_chi0_streamed(c)) != CHI0_OK) return s;
     if (c->has_real && !defer_combine) {
@@ -1484,6 +1547,14 @@ chi0_status chi0_set_band_blocks(chi0_ctx* c, int bands_per_block, int k_per_blo
   return CHI0_OK;
 }
 
+chi0_status chi0_get_pole_groups(chi0_ctx* c, int64_t* ngroups, int* grouped_contraction) {
+  if (!c) return CHI0_EINVAL;
+  if (c->plan_chi_iq < 0) return fail(c, CHI0_ESTATE, "no chi0 planned yet");
+  if (ngroups) *ngroups = c->grp_thresh > 0.0 ? c->ngroups : 0;
+  if (grouped_contraction) *grouped_contraction = c->grouped ? 1 : 0;
+  return CHI0_OK;
+}
+
 chi0_status chi0_set_pole_grouping(chi0_ctx* c, double eps_thresh) {
   if (!c) return CHI0_EINVAL;
   if (!std::isfinite(eps_thresh) || eps_thresh < 0.0)
@@ -1648,7 +1719,8 @@ void chi0_destroy(chi0_ctx* c) {
                     &c->d_err, &c->d_vsqrt, &c->d_omim, &c->d_tc, &c->d_termx, &c->d_termy,
                     &c->d_termq, &c->d_termw, &c->d_termc, &c->d_bgd, &c->d_bgperm, &c->d_bgkq,
                     &c->d_bgg0, &c->d_bgrd, &c->d_bgw, &c->d_bgP, &c->d_bgidx, &c->d_sigR, &c->d_sigWd,
-                    &c->d_sigY, &c->d_sigI, &c->d_sigRT, &c->d_dpole, &c->d_epsd, &c->d_Ublk};
+                    &c->d_sigY, &c->d_sigI, &c->d_sigRT, &c->d_dpole, &c->d_epsd, &c->d_Ublk,
+                    &c->d_tperm, &c->d_grange, &c->d_ga, &c->d_gfac};
   for (DevBuf* b : bufs) release(*b);
   for (auto& st : c->stage)
     for (cudaEvent_t e : st.ev)

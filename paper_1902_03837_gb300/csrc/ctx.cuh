@@ -99,6 +99,17 @@ struct chi0_ctx {
   // degenerate-pole grouping (Appendix B) and the double-grid frequency factor
   double grp_thresh = 0.0;             // Ha; 0: every pole its own factor
   DevBuf d_dpole;                      // [nt] pole energy of each transition's group representative
+  // grouped contraction (mixed form, groups large enough to pay): the
+  // frequency-independent group sums M_g = sum_{t in g} pref (f_m - f_n)
+  // rho_t rho_t^H from one contraction over the transitions in group order,
+  // then chi0(w) = sum_g F_g(w) M_g per frequency
+  bool grouped = false;
+  int ngroups = 0;                     // groups of the last grouping plan
+  int64_t kgrp = 0;                    // transitions in group order, each group padded to 64
+  DevBuf d_tperm;                      // [kgrp] int64 transition of each row (-1: padding)
+  DevBuf d_grange;                     // [ngroups] int2 (first k-block, k-blocks) of each group
+  DevBuf d_ga;                         // [nt] double pref (f_m - f_n)
+  DevBuf d_gfac;                       // [nwv][ngroups] float F_g(w) of the representatives
   int dg_nd = 0;                       // dense points per k; 0: off
   DevBuf d_epsd;                       // [nk][dg_nd][nb] dense-grid energies
   // self-energy kernel I (sigma.cu; its tensor-core operands in tc.cu):
@@ -147,6 +158,10 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw);
 // vkind (optional, host, [nw]): kinds of the frequency list; an entry of kind 1
 // followed by one of kind 2 is contracted once with the complex weights
 // w[v] + i w[v + 1] over the full tile grid, its chi0 written at entry v
+// grouped contraction: plan (operands in group order, partials per group and
+// tile) and launch (splits, one contraction, the per-frequency combination)
+chi0_status tc_plan_grouped(chi0_ctx* c, int ng, int nw);
+chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_freq);
 // accumulate: chi += this contraction (the transitions come in blocks)
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq = nullptr,

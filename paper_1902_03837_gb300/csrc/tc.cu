@@ -214,7 +214,8 @@ __global__ void __maxnreg__(224)
 k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
               int total_kb, int kb_per_split, int mpad, double2* __restrict__ part, int ntiles,
-              int nunits, int* __restrict__ err, int nI, int mpad_b, int f32out) {
+              int nunits, int* __restrict__ err, int nI, int mpad_b, int f32out,
+              const int2* __restrict__ ranges) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -231,6 +232,12 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
   if (*(volatile int*)(err + 1)) return;  // an earlier CTA timed out: skip the work
   // k-block range of a unit
   auto unit_range = [&](int u, int& kb0, int& nkb) {
+    if (ranges) {  // k-block range of split u / ntiles from the table (a pole group)
+      const int2 r = ranges[u / ntiles];
+      kb0 = r.x;
+      nkb = r.y;
+      return;
+    }
     kb0 = (u / ntiles) * kb_per_split;
     nkb = max(0, min(total_kb, kb0 + kb_per_split) - kb0);
   };
@@ -439,25 +446,34 @@ struct PrepOut {
   const double* wi[kPrepGroup];
 };
 
+// perm (optional): row t of the operand is transition perm[t] of R (-1: a
+// zero row), for nt rows; without it row t is transition t.
 __global__ void __launch_bounds__(256)
-k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, const __grid_constant__ PrepOut out) {
+k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, const __grid_constant__ PrepOut out,
+       const int64_t* __restrict__ perm) {
   __shared__ float tile[2 * kPI][kPT + 1];
   __shared__ float ws[kPrepGroup][kPT];   // weights converted once per transition (FP64 is slow here)
   __shared__ float wsi[kPrepGroup][kPT];  // imaginary parts of complex weights
+  __shared__ int64_t src[kPT];            // transition of each row (-1: zero row)
   const int64_t kb = blockIdx.x;
   const int64_t t0 = kb * kPT;
   const int i0 = blockIdx.y * kPI;
+  for (int tl = threadIdx.x; tl < kPT; tl += 256) {
+    const int64_t t = t0 + tl;
+    src[tl] = t < nt ? (perm ? perm[t] : t) : -1;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < ngrp * kPT; e += 256) {
     const int g = e / kPT, tl = e % kPT;
-    const int64_t t = t0 + tl;
-    ws[g][tl] = (out.wr[g] && t < nt) ? (float)out.wr[g][t] : 1.f;
-    wsi[g][tl] = (out.wi[g] && t < nt) ? (float)out.wi[g][t] : 0.f;
+    const int64_t t = src[tl];
+    ws[g][tl] = (out.wr[g] && t >= 0) ? (float)out.wr[g][t] : 1.f;
+    wsi[g][tl] = (out.wi[g] && t >= 0) ? (float)out.wi[g][t] : 0.f;
   }
   for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
     const int tl = e / kPI, il = e % kPI;
-    const int64_t t = t0 + tl;
+    const int64_t t = src[tl];
     const int i = i0 + il;
-    const float2 v = (t < nt && i < ng) ? R[t * ng + i] : make_float2(0.f, 0.f);
+    const float2 v = (t >= 0 && i < ng) ? R[t * ng + i] : make_float2(0.f, 0.f);
     tile[2 * il][tl] = v.x;
     tile[2 * il + 1][tl] = v.y;
   }
@@ -678,6 +694,140 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   return CHI0_OK;
 }
 
+namespace {
+
+// Grouped contraction, per frequency: chi[i][j] (i >= j) = sum_g F_g(w) M_g[i][j]
+// over the pole groups (Appendix B: a frequency factor per group times the
+// frequency-independent sum of the group's rho rho^* terms), M_g read from
+// the partial tiles of the group's contraction unit; up to kCombW
+// frequencies per launch, compensated FP32 sums, Hermitian mirror.
+constexpr int kCombW = 8;
+__global__ void __launch_bounds__(256)
+k_grp_combine(const double2* __restrict__ part, const float* __restrict__ F, int ngroups, int ntiles, int ng,
+              int w0, int nwc, double2* __restrict__ chi) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ng * ng) return;
+  const int i = (int)(e / ng), j = (int)(e % ng);
+  if (i < j) return;
+  const int I = i / (kBM / 2), J = j / (kBN / 2);
+  const int tile = I * (I + 1) / 2 + J;
+  const size_t off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  float sx[kCombW], sy[kCombW], cx[kCombW], cy[kCombW];
+#pragma unroll
+  for (int w = 0; w < kCombW; ++w) sx[w] = sy[w] = cx[w] = cy[w] = 0.f;
+  for (int g = 0; g < ngroups; ++g) {
+    const double2 p = part[((size_t)g * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
+    const float px = (float)p.x, py = (float)p.y;
+#pragma unroll
+    for (int w = 0; w < kCombW; ++w) {
+      if (w < nwc) {
+        const float f = F[(size_t)(w0 + w) * ngroups + g];
+        nsum(sx[w], cx[w], f * px);
+        nsum(sy[w], cy[w], f * py);
+      }
+    }
+  }
+  const size_t n2 = (size_t)ng * ng;
+#pragma unroll
+  for (int w = 0; w < kCombW; ++w) {
+    if (w < nwc) {
+      const double x = (double)sx[w] + (double)cx[w];
+      const double y = i == j ? 0.0 : (double)sy[w] + (double)cy[w];
+      double2* o = chi + (size_t)(w0 + w) * n2;
+      o[(size_t)i * ng + j] = make_double2(x, y);
+      if (i != j) o[(size_t)j * ng + i] = make_double2(x, -y);
+    }
+  }
+}
+
+}  // namespace
+
+chi0_status tc_plan_grouped(chi0_ctx* c, int ng, int nw) {
+  if (!c->tc) c->tc = new TcState();
+  TcState& t = *static_cast<TcState*>(c->tc);
+  t.mpad = (2 * ng + kBM - 1) / kBM * kBM;
+  t.kpad = c->kgrp;
+  const int nT = t.mpad / kBM;
+  t.ntiles = nT * (nT + 1) / 2;
+  t.total_kb = (int)(t.kpad / kBK);
+  t.group = 1;
+  int nsm = 148, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  t.nsm = nsm;
+  if (t.kpad / kPT > 0x7fffffff / t.mpad || (int64_t)c->ngroups * t.ntiles > 0x7fffffff)
+    return ctx_fail(c, CHI0_EUNSUPPORTED, "too many grouped transitions for one contraction");
+  const size_t opb = (size_t)t.mpad * t.kpad * 2;
+  chi0_status s;
+  DevBuf* ops[] = {&t.bh, &t.bl, &t.ah[0], &t.al[0]};
+  for (DevBuf* b : ops)
+    if ((s = ctx_ensure(c, *b, opb, "grouped operands")) != CHI0_OK) return s;
+  if ((s = ctx_ensure(c, t.part, (size_t)c->ngroups * t.ntiles * (kBM / 2) * (kBN / 2) * 16, "group sums")) !=
+      CHI0_OK)
+    return s;
+  if (!make_map(&t.m_ah[0], t.ah[0].p, t.kpad, t.mpad) || !make_map(&t.m_al[0], t.al[0].p, t.kpad, t.mpad) ||
+      !make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
+    return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
+  cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
+  (void)nw;
+  return CHI0_OK;
+}
+
+chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_freq) {
+  if (!c->tc) return ctx_fail(c, CHI0_ESTATE, "grouped contraction not planned");
+  TcState& t = *static_cast<TcState*>(c->tc);
+  const int ng = c->cfg.ng, nw = c->nwv;
+  const int64_t n2 = (int64_t)ng * ng;
+  const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
+  const int64_t* perm = (const int64_t*)c->d_tperm.p;
+  // operands in group order: B = rho, A = pref (f_m - f_n) rho (frequency independent)
+  PrepOut ob{}, oa{};
+  ob.hi[0] = (__nv_bfloat16*)t.bh.p;
+  ob.lo[0] = (__nv_bfloat16*)t.bl.p;
+  oa.hi[0] = (__nv_bfloat16*)t.ah[0].p;
+  oa.lo[0] = (__nv_bfloat16*)t.al[0].p;
+  oa.wr[0] = (const double*)c->d_ga.p;
+  stage_begin(c, CHI0_STAGE_WEIGHTS);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, t.kpad, ng, t.mpad, ob, perm);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, t.kpad, ng, t.mpad, oa, perm);
+  stage_end(c, CHI0_STAGE_WEIGHTS, 2);
+  // one unit per (tile, group): the group sums M_g, tile by tile
+  const int nunits = t.ntiles * c->ngroups;
+  stage_begin(c, CHI0_STAGE_CONTRACT);
+  k_herk_bf16x3<<<(unsigned)std::min(nunits, std::max(1, t.nsm)), kThreads, kSmemBytes, c->st>>>(
+      t.m_ah[0], t.m_al[0], t.m_bh, t.m_bl, t.total_kb, t.total_kb, t.mpad, (double2*)t.part.p, t.ntiles, nunits,
+      (int*)c->d_err.p, 0, t.mpad, 0, (const int2*)c->d_grange.p);
+  stage_end(c, CHI0_STAGE_CONTRACT, 1);
+  // chi0 at every frequency from the group sums and the groups' factors
+  const unsigned cgrid = (unsigned)((n2 + 255) / 256);
+  int nlaunch = 0;
+  stage_begin(c, CHI0_STAGE_REDUCE);
+  for (int w0 = 0; w0 < nw; w0 += kCombW, ++nlaunch) {
+    const int nwc = std::min(kCombW, nw - w0);
+    k_grp_combine<<<cgrid, 256, 0, c->st>>>((const double2*)t.part.p, (const float*)c->d_gfac.p, c->ngroups,
+                                            t.ntiles, ng, w0, nwc, chi);
+    if (ev_freq)
+      for (int w = w0; w < w0 + nwc; ++w) cudaEventRecord(ev_freq[w], c->st);
+  }
+  stage_end(c, CHI0_STAGE_REDUCE, nlaunch);
+  const double tile_bytes = (double)(kBM / 2) * (kBN / 2) * 16;
+  c->stage[CHI0_STAGE_WEIGHTS].bytes = 2.0 * (double)c->nt * ng * 8 + 2.0 * 4.0 * t.mpad * t.kpad;
+  c->stage[CHI0_STAGE_CONTRACT].bytes = 8.0 * t.mpad * t.kpad + (double)nunits * tile_bytes;
+  // the work done: one Hermitian contraction over the transitions in group
+  // order (not one per frequency), then the combination per frequency
+  c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)t.kpad;
+  c->stage[CHI0_STAGE_REDUCE].flops = 2.0 * (double)ng * (ng + 1) * (double)c->ngroups * nw;
+  c->stage[CHI0_STAGE_REDUCE].bytes = (double)nlaunch * nunits * tile_bytes + (double)n2 * nw * 16;
+  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)t.kpad * t.ntiles;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
+  return CHI0_OK;
+}
+
 chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, int ng, int nw,
                       double2* chi, const cudaEvent_t* ev_freq, const cudaEvent_t* ev_prep,
                       const BgApply* bg, const int* vkind, int accumulate) {
@@ -691,7 +841,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
   ob.hi[0] = (__nv_bfloat16*)t.bh.p;
   ob.lo[0] = (__nv_bfloat16*)t.bl.p;
   stage_begin(c, CHI0_STAGE_WEIGHTS);
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, 1, nt, ng, t.mpad, ob);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, 1, nt, ng, t.mpad, ob, nullptr);
   stage_end(c, CHI0_STAGE_WEIGHTS, 1);
   // jobs: an entry of the frequency list with real weights is one Hermitian
   // contraction (lower-triangle tiles); a real-axis frequency (entries of
@@ -723,7 +873,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       oa.wi[g] = jb.cplx ? w + (size_t)(jb.v + 1) * nt : nullptr;
     }
     stage_begin(c, CHI0_STAGE_WEIGHTS);
-    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, gw, nt, ng, t.mpad, oa);
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, gw, nt, ng, t.mpad, oa, nullptr);
     stage_end(c, CHI0_STAGE_WEIGHTS, 1);
     if (ev_prep)
       for (int g = 0; g < gw; ++g) {
@@ -737,12 +887,12 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       if (jb.cplx) {
         k_herk_bf16x3<<<hgrid_f, kThreads, kSmemBytes, c->st>>>(
             t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
-            nunits_f, (int*)c->d_err.p, nT, t.mpad, 0);
+            nunits_f, (int*)c->d_err.p, nT, t.mpad, 0, nullptr);
         ++nfull;
       } else {
         k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
             t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
-            nunits, (int*)c->d_err.p, 0, t.mpad, 0);
+            nunits, (int*)c->d_err.p, 0, t.mpad, 0, nullptr);
         ++nherm;
       }
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
@@ -826,12 +976,12 @@ chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
   PrepOut ob{};
   ob.hi[0] = (__nv_bfloat16*)t.bh.p;
   ob.lo[0] = (__nv_bfloat16*)t.bl.p;
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, ob);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, ob, nullptr);
   PrepOut oa{};
   oa.hi[0] = (__nv_bfloat16*)t.ah[0].p;
   oa.lo[0] = (__nv_bfloat16*)t.al[0].p;
   oa.wr[0] = (const double*)c->d_w.p;
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, oa);
+  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, oa, nullptr);
   const size_t cap = t.part.bytes / ((size_t)(kBM / 2) * (kBN / 2) * 16);
   const int base_split = (t.total_kb + t.kbpc - 1) / t.kbpc;
   int best_kbpc = t.kbpc, best_n = t.nchunks;
@@ -852,7 +1002,7 @@ chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
       cudaEventRecord(e0, c->st);
       k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[0], t.m_al[0], t.m_bh, t.m_bl, t.total_kb, kbpc,
                                                             t.mpad, (double2*)t.part.p, t.ntiles, nunits,
-                                                            (int*)c->d_err.p, 0, t.mpad, 0);
+                                                            (int*)c->d_err.p, 0, t.mpad, 0, nullptr);
       cudaEventRecord(e1, c->st);
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
         cudaGetLastError();
@@ -1030,7 +1180,7 @@ cudaError_t sig_tc_contract(chi0_ctx* c, float2* Y) {
   const unsigned grid = (unsigned)std::min(ntiles, t.nsm);
   k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah, t.m_al, t.m_bh, t.m_bl, total_kb, total_kb,
                                                         t.mpad_a, reinterpret_cast<double2*>(Y), ntiles, ntiles,
-                                                        (int*)c->d_err.p, t.nI, (int)t.mpad_b, 1);
+                                                        (int*)c->d_err.p, t.nI, (int)t.mpad_b, 1, nullptr);
   return cudaGetLastError();
 }
 

@@ -49,6 +49,7 @@ class SystemSpec:
     seed: int = 1
     coef_dtype: str = "c128"             # "c128" or "c64"
     spin_factor: float = 2.0
+    flat_bands: bool = False             # True: every k gets the band energies of k = 0
 
 
 @dataclasses.dataclass
@@ -208,6 +209,10 @@ def make_system(spec: SystemSpec) -> System:
         coef[jk, :, : gp.shape[0]] = np.conj(c[:, src])
         eps[jk] = e
         done[ik] = done[jk] = True
+    if spec.flat_bands:
+        # dispersionless bands: the pole energies eps_m - eps_n repeat at every
+        # k, the degenerate case of Appendix B's pole grouping
+        eps[:] = eps[0][None, :]
     occ = _occupations(spec, eps)
     lattice = spec.a * np.eye(3)
     return System(

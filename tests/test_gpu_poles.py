@@ -124,3 +124,62 @@ def test_switch_off_and_argument_checks(lib):
     ctx.build_chi0(0, chi)
     ctx.close()
     assert np.array_equal(chi, plain)
+
+
+def _flat(dtype, split, seed=95):
+    """64 k points whose poles repeat at every k up to +-split (Ha): 27 pole
+    groups of 64 transitions, large enough for the grouped contraction."""
+    s = make_system(cfg_tiny(seed=seed, kgrid=(4, 4, 4), q_frac=((0.25, 0.5, 0.0),), fft=(18, 18, 18), ng=40,
+                             n_occ=3, n_bands=12, npw_target=50, a=8.0, freqs=(0.02j, 0.3j, 1.5j, 6.0j),
+                             eta=0.0, coef_dtype=dtype))
+    return _near_degenerate(s, split) if split > 0 else dataclasses.replace(
+        s, eps=np.repeat(s.eps[:1], s.nk, axis=0))
+
+
+def _chi_groups(lib, s, prec, thresh):
+    import torch
+    ctx = lib.Chi0.for_system(s, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+    ctx.load_system(s)
+    if thresh:
+        ctx.set_pole_grouping(thresh)
+    ctx.compute_rho(0)
+    chi = torch.zeros((s.freqs.size, s.ng, s.ng), dtype=torch.complex128, device="cuda")
+    inv = torch.zeros_like(chi)
+    ctx.build_invert(0, inv, chi)
+    ctx.synchronize()
+    groups = ctx.pole_groups()
+    ctx.close()
+    return chi.cpu().numpy(), inv.cpu().numpy(), groups
+
+
+def test_grouped_contraction_vs_oracle(lib):
+    """Large pole groups (splitting 1e-6 Ha below the 1e-4 Ha threshold): the
+    mixed form builds chi0 from the frequency-independent group sums; chi0 and
+    eps~^-1 equal the oracle's grouped result (1e-5) and the FP64 form's
+    per-transition grouped weights (1e-5)."""
+    s = _flat("c64", 1e-6)
+    G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
+    chi, inv, (ngr, grouped) = _chi_groups(lib, s, 1, 1e-4)
+    assert grouped and ngr == 27
+    want = O.chi0_grouped(s, 0, G, s.freqs, s.eta, 1e-4)
+    qg = O.qg_norms(s.spec.a, s.q_frac[0], G)
+    want_inv = np.stack([O.eps_inv_gauss_jordan(c, qg) for c in want])
+    assert _rel(chi, want) < 1e-5
+    assert _rel(inv, want_inv) < 1e-5
+    assert np.abs(chi - np.conj(np.transpose(chi, (0, 2, 1)))).max() == 0.0
+    s64 = dataclasses.replace(s, coef=s.coef.astype(np.complex128))
+    chi64, _, (ngr64, grouped64) = _chi_groups(lib, s64, 0, 1e-4)
+    assert ngr64 == 27 and not grouped64
+    assert _rel(chi, chi64) < 1e-5
+
+
+def test_grouped_contraction_exact_degeneracy(lib):
+    """Poles exactly degenerate across k: grouping changes no factor, so the
+    grouped contraction reproduces the plain chi0 and the oracle."""
+    s = _flat("c64", 0.0)
+    G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
+    chi, _, (ngr, grouped) = _chi_groups(lib, s, 1, 1e-8)
+    plain, _, (n0, g0) = _chi_groups(lib, s, 1, 0.0)
+    assert grouped and ngr == 27 and n0 == 0 and not g0
+    assert _rel(chi, plain) < 3e-6
+    assert _rel(chi, O.chi0_tr(s, 0, G, s.freqs, s.eta)) < 1e-5
