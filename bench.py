@@ -61,7 +61,7 @@ def whole_job_tflops(world, flops_per_step, ms_per_step):
 
 
 # stage -> (binding roof, unit, kernel)
-STAGE_ROOF = {"contract": ("tensor", "TFLOP/s", "k_herk_bf16x3"), "rho": ("alu", "TFLOP/s", "k_rho_pairs"),
+STAGE_ROOF = {"contract": ("tensor", "TFLOP/s", "k_herk_wide"), "rho": ("alu", "TFLOP/s", "k_rho_pairs"),
               "wf_grid": ("alu", "TFLOP/s", "k_wf_to_mixed"), "dyson": ("fp64", "TFLOP/s", "k_gj_update"),
               "weights": ("hbm", "GB/s", "k_prep"), "reduce": ("hbm", "GB/s", "k_tc_reduce")}
 # FP32 FMA: 152 SMs x 128 lanes x 2 flop x 1.93 GHz (the clock seen under this load)
@@ -74,7 +74,7 @@ FP64_PEAK, FP64_SRC = 1.25, "FP64 nominal (GB300)"
 #   traffic: <kernel> | <workload> | <bytes per launch> | <source file> <sha256 prefix> | <how>
 # A figure is used only while the kernel's source file still has the hash it
 # had when the counters were taken; after any change it reads as null.
-KERNEL_SOURCE = {"k_herk_bf16x3": "tc.cu", "k_prep": "tc.cu", "k_rho_pairs": "rho.cu",
+KERNEL_SOURCE = {"k_herk_bf16x3": "tc.cu", "k_herk_wide": "tc.cu", "k_prep": "tc.cu", "k_rho_pairs": "rho.cu",
                  "k_wf_to_mixed": "rho.cu", "k_gj_update": "dyson.cu", "k_chi0_fp64": "chi0_fp64.cu"}
 
 
@@ -648,13 +648,16 @@ def run_ours(args, rank, world, dist):
         # products actually issued (3 per k-step over the lower-triangle tiles)
         achieved = st_flops[dom] / (per_step_ms[dom] * 1e-3) / 1e12
         peak, psrc = pk["bf16_tflops_sustained"], f"BF16 dense sustained ({pk['source']})"
-        mpad = -(-2 * ng // 128) * 128
+        mpad = -(-2 * ng // 256) * 256
         kpad = -(-nt // 64) * 64
-        nT = mpad // 128
-        # an imaginary frequency is one Hermitian contraction (lower-triangle
-        # tiles), a real one one contraction with complex weights (every tile)
-        tiles = nT * nT if args.real_axis else nT * (nT + 1) // 2
-        issued = 3 * 2 * 128 * 128 * tiles * kpad * nw
+        nI, nJ = mpad // 128, mpad // 256
+        # an imaginary frequency is one Hermitian contraction (128 x 256
+        # tiles covering the lower triangle), a real one one contraction with
+        # complex weights (every 128 x 128 tile)
+        if args.real_axis:
+            issued = 3 * 2 * 128 * 128 * nI * nI * kpad * nw
+        else:
+            issued = 3 * 2 * 128 * 256 * (nI * nJ - nJ * (nJ - 1)) * kpad * nw
         extra = {"issued_tflops": issued / (per_step_ms[dom] * 1e-3) / 1e12,
                  "issued_frac": issued / (per_step_ms[dom] * 1e-3) / 1e12 / peak}
     elif bound == "fp64":

@@ -229,7 +229,12 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (*(volatile int*)(err + 1)) return;  // an earlier CTA timed out: skip the work
+  {  // an earlier CTA timed out: skip the work (one read, so the whole CTA agrees)
+    volatile int* skip = reinterpret_cast<volatile int*>(tmem_slot + 2);
+    if (threadIdx.x == 0) *skip = *(volatile int*)(err + 1);
+    __syncthreads();
+    if (*skip) return;
+  }
   // k-block range of a unit
   auto unit_range = [&](int u, int& kb0, int& nkb) {
     if (ranges) {  // k-block range of split u / ntiles from the table (a pole group)
@@ -426,6 +431,253 @@ k_herk_bf16x3(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__
   }
 }
 
+// ---- wide tiles: 128 rows of A x 256 rows of B per unit ---------------------
+// The Hermitian contraction with N = 256 per MMA: each k-block stages Ah, Al
+// (128 rows) and Bh, Bl (256 rows, two TMA boxes each) and issues 12
+// tcgen05.mma of 128 x 256 x 16, so one operand byte feeds twice the products
+// of a 128 x 128 tile (half the shared-memory and L2 traffic per product of
+// A, and twice the work per stage in flight).  Two stages of 96 KB.  The
+// accumulators take all 512 TMEM columns (two of 256, ping-pong); eight
+// epilogue warps drain them, two per TMEM lane quadrant, each holding the
+// compensated sums of 128 of the 256 columns (as many as the narrow kernel's
+// four).  Warps 0..3 (producer, MMA issuer, two idle) give registers to the
+// epilogue warpgroups: 384 threads launched at 144 registers (55,296), then
+// 4 x 32 x 40 + 8 x 32 x 192 = 54,272 after the hand-over, which leaves a
+// 128-thread, 64-register Dyson block room beside it (10,240 registers,
+// 2,816 per sub-partition).
+// Tiles: (I, J) with I in [2J, nI), nI = mpad / 128 row tiles of A and nJ =
+// mpad / 256 column tiles of B (mpad a multiple of 256): every real entry
+// (r, c) with r >= c lies in one of them.  Tile index = sum_{J' < J} (nI - 2J')
+// + (I - 2J).  Partial output: 64 complex rows x 128 complex columns per
+// unit.
+constexpr int kWN = 256;                          // tile cols (real)
+constexpr int kWStages = 2;
+constexpr int kWTileA = kBM * kBK * 2;            // 16 KB
+constexpr int kWTileB = kWN * kBK * 2;            // 32 KB
+constexpr int kWStageBytes = 2 * kWTileA + 2 * kWTileB;   // 96 KB
+constexpr int kWSmemBytes = kWStages * kWStageBytes + 1024 + 256;
+constexpr int kWThreads = 384;
+constexpr int kWPart = (kBM / 2) * (kWN / 2);     // complex entries of a partial tile
+
+__device__ __forceinline__ void wide_decode(int tile, int nI, int& I, int& J) {
+  int J0 = 0, base = 0;
+  while (base + (nI - 2 * J0) <= tile) {
+    base += nI - 2 * J0;
+    ++J0;
+  }
+  J = J0;
+  I = 2 * J0 + (tile - base);
+}
+
+__device__ __forceinline__ void setmaxnreg_dec40() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 40;" ::: "memory");
+}
+__device__ __forceinline__ void setmaxnreg_inc192() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 192;" ::: "memory");
+}
+
+__global__ void __maxnreg__(144)
+k_herk_wide(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+            const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl, int total_kb,
+            int kb_per_split, int mpad, double2* __restrict__ part, int ntiles, int nunits,
+            int* __restrict__ err, int nI, const int2* __restrict__ ranges) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kWStages * kWStageBytes);
+  const uint32_t bar_full = smem_u32(bars);                    // [kWStages]
+  const uint32_t bar_empty = smem_u32(bars + kWStages);        // [kWStages]
+  const uint32_t bar_accf = smem_u32(bars + 2 * kWStages);     // [2] accumulator full
+  const uint32_t bar_acce = smem_u32(bars + 2 * kWStages + 2); // [2] accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kWStages + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {  // an earlier CTA timed out: skip the work (one read, so the whole CTA agrees)
+    volatile int* skip = reinterpret_cast<volatile int*>(tmem_slot + 2);
+    if (threadIdx.x == 0) *skip = *(volatile int*)(err + 1);
+    __syncthreads();
+    if (*skip) return;
+  }
+  auto unit_range = [&](int u, int& kb0, int& nkb) {
+    if (ranges) {
+      const int2 r = ranges[u / ntiles];
+      kb0 = r.x;
+      nkb = r.y;
+      return;
+    }
+    kb0 = (u / ntiles) * kb_per_split;
+    nkb = max(0, min(total_kb, kb0 + kb_per_split) - kb0);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kWStages; ++st) {
+      mbar_init(bar_full + 8 * st, 1);
+      mbar_init(bar_empty + 8 * st, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_accf + 8 * b, 1);
+      mbar_init(bar_acce + 8 * b, 8);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_ah) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_al) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_bh) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_bl) : "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 2 * kWN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp < 4) {
+    setmaxnreg_dec40();
+    if (warp == 0 && lane == 0) {
+      // ---------------- TMA producer
+      int gk = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int I, J, kb0, nkb;
+        wide_decode(u % ntiles, nI, I, J);
+        unit_range(u, kb0, nkb);
+        for (int k = 0; k < nkb; ++k, ++gk) {
+          const int st = gk % kWStages;
+          const uint32_t ph = (uint32_t)((gk / kWStages) & 1);
+          if (!mbar_wait(bar_empty + 8 * st, ph ^ 1u, abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sb = base + st * kWStageBytes;
+          mbar_expect_tx(bar_full + 8 * st, kWStageBytes);
+          const int row = (kb0 + k) * mpad;
+          tma_load_2d(sb, &tm_ah, 0, row + I * kBM, bar_full + 8 * st);
+          tma_load_2d(sb + kWTileA, &tm_al, 0, row + I * kBM, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA, &tm_bh, 0, row + J * kWN, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA + kWTileA, &tm_bh, 0, row + J * kWN + kBM, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA + kWTileB, &tm_bl, 0, row + J * kWN, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA + kWTileB + kWTileA, &tm_bl, 0, row + J * kWN + kBM, bar_full + 8 * st);
+        }
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(kBM, kWN);
+      int gk = 0, gsc = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int kb0, nkb;
+        unit_range(u, kb0, nkb);
+        const int nsub = (nkb + kSubKB - 1) / kSubKB;
+        int k = 0;
+        for (int sc = 0; sc < nsub; ++sc, ++gsc) {
+          const int b = gsc & 1;
+          if (!mbar_wait(bar_acce + 8 * b, (uint32_t)(((gsc >> 1) & 1) ^ 1), abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc = tmem + (uint32_t)(b * kWN);
+          const int kend = min(nkb, (sc + 1) * kSubKB);
+          for (int kk0 = 0; k < kend; ++k, ++kk0, ++gk) {
+            const int st = gk % kWStages;
+            const uint32_t ph = (uint32_t)((gk / kWStages) & 1);
+            if (!mbar_wait(bar_full + 8 * st, ph, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sb = base + st * kWStageBytes;
+            const uint64_t dah = desc_sw128(sb);
+            const uint64_t dal = desc_sw128(sb + kWTileA);
+            const uint64_t dbh = desc_sw128(sb + 2 * kWTileA);
+            const uint64_t dbl = desc_sw128(sb + 2 * kWTileA + kWTileB);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+              const uint64_t off = (uint64_t)((kk * 32) >> 4);
+              umma_bf16(acc, dah + off, dbh + off, idesc, (kk0 > 0 || kk > 0) ? 1u : 0u);
+              umma_bf16(acc, dah + off, dbl + off, idesc, 1u);
+              umma_bf16(acc, dal + off, dbh + off, idesc, 1u);
+            }
+            umma_commit(bar_empty + 8 * st);
+          }
+          if (!ok) break;
+          umma_commit(bar_accf + 8 * b);
+        }
+      }
+    }
+  } else {
+    setmaxnreg_inc192();
+    // ---------------- epilogue: warps 4..11; TMEM lane quadrant warp % 4,
+    // column half (warp - 4) / 4 of the 256 accumulator columns
+    const int q = warp & 3;
+    const int hcol = (warp - 4) >> 2;
+    const bool odd = (lane & 1) != 0;
+    int gsc = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      int kb0, nkb;
+      unit_range(u, kb0, nkb);
+      const int nsub = (nkb + kSubKB - 1) / kSubKB;
+      float accs[32][2], accc[32][2];
+#pragma unroll
+      for (int e = 0; e < 32; ++e) accs[e][0] = accs[e][1] = accc[e][0] = accc[e][1] = 0.f;
+      for (int sc = 0; sc < nsub; ++sc, ++gsc) {
+        const int b = gsc & 1;
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(bar_accf + 8 * b, (uint32_t)((gsc >> 1) & 1), abort_flag, err) ? 1 : 0) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kWN + hcol * kBN);
+#pragma unroll
+        for (int cb = 0; cb < kBN / 16; ++cb) {
+          uint32_t v[16];
+          tmem_ld16(acc + (uint32_t)(cb * 16), v);
+          float recv[8];
+#pragma unroll
+          for (int k2 = 0; k2 < 8; ++k2) {
+            const float send = __uint_as_float(odd ? v[k2] : v[8 + k2]);
+            recv[k2] = __shfl_xor_sync(0xffffffffu, send, 1);
+          }
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const float r0c0 = odd ? recv[2 * jj] : __uint_as_float(v[2 * jj]);
+            const float r0c1 = odd ? recv[2 * jj + 1] : __uint_as_float(v[2 * jj + 1]);
+            const float r1c0 = odd ? __uint_as_float(v[8 + 2 * jj]) : recv[2 * jj];
+            const float r1c1 = odd ? __uint_as_float(v[9 + 2 * jj]) : recv[2 * jj + 1];
+            const int e = cb * 4 + jj;
+            nsum(accs[e][0], accc[e][0], r0c0 + r1c1);
+            nsum(accs[e][1], accc[e][1], r1c0 - r0c1);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acce + 8 * b) : "memory");
+      }
+      if (!ok) break;
+      const int il = (q * 32 + lane) >> 1;  // complex row of the tile
+      double2* out = part + (size_t)u * kWPart + (size_t)il * (kWN / 2) + hcol * (kBN / 2) + (odd ? 4 : 0);
+#pragma unroll
+      for (int cb = 0; cb < kBN / 16; ++cb)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int e = cb * 4 + jj;
+          out[cb * 8 + jj] = make_double2((double)accs[e][0] + (double)accc[e][0],
+                                          (double)accs[e][1] + (double)accc[e][1]);
+        }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * kWN);
+  }
+}
+
 // hi/lo BF16 split of the real operand in k-blocked layout: element (m, t),
 // m = 2 i + c, sits at [t / 64][m][t % 64] (each block of 64 transitions holds
 // all rows, 128 bytes per row), so one 128-row TMA box is one contiguous 16 KB
@@ -512,18 +764,33 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
 }
 
 // chi[i][j] (i >= j) = sum over chunks of the partials (FP64), mirrored.
+// Position of the complex entry (i, j), i >= j, among the Hermitian
+// contraction's partial tiles: narrow 64 x 64 tiles in lower-triangle order,
+// or wide 64 x 128 tiles (I = i / 64, J = j / 128, I >= 2J) column by column.
+__device__ __forceinline__ void herm_pos(int i, int j, int wide, int nI, int& tile, size_t& off) {
+  if (wide) {
+    const int I = i / (kBM / 2), J = j / (kWN / 2);
+    tile = J * nI - J * (J - 1) + (I - 2 * J);
+    off = (size_t)(i % (kBM / 2)) * (kWN / 2) + (j % (kWN / 2));
+  } else {
+    const int I = i / (kBM / 2), J = j / (kBN / 2);
+    tile = I * (I + 1) / 2 + J;
+    off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  }
+}
+
 __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int ntiles, int ng,
-                            double2* __restrict__ chi, int accumulate) {
+                            double2* __restrict__ chi, int accumulate, int wide, int nI, int tile_elems) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
   const int i = (int)(e / ng), j = (int)(e % ng);
   if (i < j) return;
-  const int I = i / (kBM / 2), J = j / (kBN / 2);
-  const int tile = I * (I + 1) / 2 + J;
-  const size_t off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  int tile;
+  size_t off;
+  herm_pos(i, j, wide, nI, tile, off);
   double sx = 0.0, sy = 0.0;
   for (int c = 0; c < nchunks; ++c) {
-    const double2 v = part[((size_t)c * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
+    const double2 v = part[((size_t)c * ntiles + tile) * tile_elems + off];
     sx += v.x;
     sy += v.y;
   }
@@ -567,7 +834,39 @@ struct TcState {
   int ntiles_f = 0, kbpc_f = 0, nchunks_f = 0;   // full tile grid (complex weights)
   int group = 1;  // frequencies per operand-split pass (A buffers in use)
   int nsm = 1;    // persistent contraction grid
+  // Hermitian contraction: wide tiles (128 x 256, k_herk_wide) or narrow ones
+  // (128 x 128, k_herk_bf16x3); nI row tiles of 128 (and nJ column tiles of
+  // 256 when wide); tile_elems complex entries per partial tile
+  int wide = 1, nI = 0, nJ = 0, tile_elems = (kBM / 2) * (kBN / 2);
 };
+
+// Tile layout of the Hermitian contraction for an operand of mpad rows.
+void herm_tiles(TcState& t) {
+  t.nI = t.mpad / kBM;
+  if (t.wide) {
+    t.nJ = t.mpad / kWN;
+    t.ntiles = t.nI * t.nJ - t.nJ * (t.nJ - 1);
+    t.tile_elems = kWPart;
+  } else {
+    t.nJ = t.nI;
+    t.ntiles = t.nI * (t.nI + 1) / 2;
+    t.tile_elems = (kBM / 2) * (kBN / 2);
+  }
+}
+
+// One Hermitian contraction launch (lower-triangle tiles x transition splits)
+cudaError_t launch_herm(chi0_ctx* c, TcState& t, int g, int kbpc, int nunits, const int2* ranges) {
+  const unsigned grid = (unsigned)std::min(nunits, std::max(1, t.nsm));
+  if (t.wide)
+    k_herk_wide<<<grid, kWThreads, kWSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, kbpc,
+                                                          t.mpad, (double2*)t.part.p, t.ntiles, nunits,
+                                                          (int*)c->d_err.p, t.nI, ranges);
+  else
+    k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, kbpc,
+                                                          t.mpad, (double2*)t.part.p, t.ntiles, nunits,
+                                                          (int*)c->d_err.p, 0, t.mpad, 0, ranges);
+  return cudaGetLastError();
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -600,10 +899,11 @@ bool make_map(CUtensorMap* m, void* ptr, int64_t kpad, int mpad) {
 chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   if (!c->tc) c->tc = new TcState();
   TcState& t = *static_cast<TcState*>(c->tc);
-  t.mpad = (2 * ng + kBM - 1) / kBM * kBM;
+  t.wide = 1;
+  t.mpad = (2 * ng + kWN - 1) / kWN * kWN;   // a multiple of the wide tile's 256 columns
   t.kpad = (nt + kBK - 1) / kBK * kBK;
   const int nT = t.mpad / kBM;
-  t.ntiles = nT * (nT + 1) / 2;
+  herm_tiles(t);
   t.total_kb = (int)(t.kpad / kBK);
   // split the transitions so that the grid fills whole waves of one CTA per SM
   int nsm = 148;
@@ -645,9 +945,9 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   // a batch problem (group_cap > 0) keeps room for twice the planned
   // partials, for the split candidates of tc_tune_split
   const size_t room = c->group_cap > 0 ? 2 : 1;
-  const size_t nparts = std::max((size_t)t.nchunks * t.ntiles * room,
-                                  c->has_real ? (size_t)t.nchunks_f * t.ntiles_f : (size_t)0);
-  if ((s = ctx_ensure(c, t.part, nparts * (kBM / 2) * (kBN / 2) * 16, "chunk partials")) != CHI0_OK)
+  const size_t nbytes = std::max((size_t)t.nchunks * t.ntiles * room * t.tile_elems,
+                                  c->has_real ? (size_t)t.nchunks_f * t.ntiles_f * (kBM / 2) * (kBN / 2) : (size_t)0);
+  if ((s = ctx_ensure(c, t.part, nbytes * 16, "chunk partials")) != CHI0_OK)
     return s;
   // A buffers for up to kPrepGroup frequencies, as far as half of the free
   // device memory allows (one pair is always needed)
@@ -674,6 +974,11 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_wide, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
   // The whole shared-memory carveout on every SM this path touches, so that
   // an SM running a contraction CTA (193 KB) keeps room for the small blocks
   // of the Dyson step of the previous frequency (a carveout sized to the CTA
@@ -704,19 +1009,19 @@ namespace {
 constexpr int kCombW = 8;
 __global__ void __launch_bounds__(256)
 k_grp_combine(const double2* __restrict__ part, const float* __restrict__ F, int ngroups, int ntiles, int ng,
-              int w0, int nwc, double2* __restrict__ chi) {
+              int w0, int nwc, double2* __restrict__ chi, int wide, int nI, int tile_elems) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
   const int i = (int)(e / ng), j = (int)(e % ng);
   if (i < j) return;
-  const int I = i / (kBM / 2), J = j / (kBN / 2);
-  const int tile = I * (I + 1) / 2 + J;
-  const size_t off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  int tile;
+  size_t off;
+  herm_pos(i, j, wide, nI, tile, off);
   float sx[kCombW], sy[kCombW], cx[kCombW], cy[kCombW];
 #pragma unroll
   for (int w = 0; w < kCombW; ++w) sx[w] = sy[w] = cx[w] = cy[w] = 0.f;
   for (int g = 0; g < ngroups; ++g) {
-    const double2 p = part[((size_t)g * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
+    const double2 p = part[((size_t)g * ntiles + tile) * tile_elems + off];
     const float px = (float)p.x, py = (float)p.y;
 #pragma unroll
     for (int w = 0; w < kCombW; ++w) {
@@ -745,10 +1050,10 @@ k_grp_combine(const double2* __restrict__ part, const float* __restrict__ F, int
 chi0_status tc_plan_grouped(chi0_ctx* c, int ng, int nw) {
   if (!c->tc) c->tc = new TcState();
   TcState& t = *static_cast<TcState*>(c->tc);
-  t.mpad = (2 * ng + kBM - 1) / kBM * kBM;
+  t.wide = 1;
+  t.mpad = (2 * ng + kWN - 1) / kWN * kWN;
   t.kpad = c->kgrp;
-  const int nT = t.mpad / kBM;
-  t.ntiles = nT * (nT + 1) / 2;
+  herm_tiles(t);
   t.total_kb = (int)(t.kpad / kBK);
   t.group = 1;
   int nsm = 148, dev = 0;
@@ -762,8 +1067,7 @@ chi0_status tc_plan_grouped(chi0_ctx* c, int ng, int nw) {
   DevBuf* ops[] = {&t.bh, &t.bl, &t.ah[0], &t.al[0]};
   for (DevBuf* b : ops)
     if ((s = ctx_ensure(c, *b, opb, "grouped operands")) != CHI0_OK) return s;
-  if ((s = ctx_ensure(c, t.part, (size_t)c->ngroups * t.ntiles * (kBM / 2) * (kBN / 2) * 16, "group sums")) !=
-      CHI0_OK)
+  if ((s = ctx_ensure(c, t.part, (size_t)c->ngroups * t.ntiles * t.tile_elems * 16, "group sums")) != CHI0_OK)
     return s;
   if (!make_map(&t.m_ah[0], t.ah[0].p, t.kpad, t.mpad) || !make_map(&t.m_al[0], t.al[0].p, t.kpad, t.mpad) ||
       !make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
@@ -771,6 +1075,11 @@ chi0_status tc_plan_grouped(chi0_ctx* c, int ng, int nw) {
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_herk_wide, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   (void)nw;
@@ -798,9 +1107,7 @@ chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_f
   // one unit per (tile, group): the group sums M_g, tile by tile
   const int nunits = t.ntiles * c->ngroups;
   stage_begin(c, CHI0_STAGE_CONTRACT);
-  k_herk_bf16x3<<<(unsigned)std::min(nunits, std::max(1, t.nsm)), kThreads, kSmemBytes, c->st>>>(
-      t.m_ah[0], t.m_al[0], t.m_bh, t.m_bl, t.total_kb, t.total_kb, t.mpad, (double2*)t.part.p, t.ntiles, nunits,
-      (int*)c->d_err.p, 0, t.mpad, 0, (const int2*)c->d_grange.p);
+  launch_herm(c, t, 0, t.total_kb, nunits, (const int2*)c->d_grange.p);
   stage_end(c, CHI0_STAGE_CONTRACT, 1);
   // chi0 at every frequency from the group sums and the groups' factors
   const unsigned cgrid = (unsigned)((n2 + 255) / 256);
@@ -809,12 +1116,12 @@ chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_f
   for (int w0 = 0; w0 < nw; w0 += kCombW, ++nlaunch) {
     const int nwc = std::min(kCombW, nw - w0);
     k_grp_combine<<<cgrid, 256, 0, c->st>>>((const double2*)t.part.p, (const float*)c->d_gfac.p, c->ngroups,
-                                            t.ntiles, ng, w0, nwc, chi);
+                                            t.ntiles, ng, w0, nwc, chi, t.wide, t.nI, t.tile_elems);
     if (ev_freq)
       for (int w = w0; w < w0 + nwc; ++w) cudaEventRecord(ev_freq[w], c->st);
   }
   stage_end(c, CHI0_STAGE_REDUCE, nlaunch);
-  const double tile_bytes = (double)(kBM / 2) * (kBN / 2) * 16;
+  const double tile_bytes = (double)t.tile_elems * 16;
   c->stage[CHI0_STAGE_WEIGHTS].bytes = 2.0 * (double)c->nt * ng * 8 + 2.0 * 4.0 * t.mpad * t.kpad;
   c->stage[CHI0_STAGE_CONTRACT].bytes = 8.0 * t.mpad * t.kpad + (double)nunits * tile_bytes;
   // the work done: one Hermitian contraction over the transitions in group
@@ -822,7 +1129,7 @@ chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_f
   c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)t.kpad;
   c->stage[CHI0_STAGE_REDUCE].flops = 2.0 * (double)ng * (ng + 1) * (double)c->ngroups * nw;
   c->stage[CHI0_STAGE_REDUCE].bytes = (double)nlaunch * nunits * tile_bytes + (double)n2 * nw * 16;
-  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)t.kpad * t.ntiles;
+  c->tc_issued_flops = 3.0 * 2.0 * kBM * (t.wide ? kWN : kBN) * (double)t.kpad * t.ntiles;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
@@ -890,9 +1197,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
             nunits_f, (int*)c->d_err.p, nT, t.mpad, 0, nullptr);
         ++nfull;
       } else {
-        k_herk_bf16x3<<<hgrid, kThreads, kSmemBytes, c->st>>>(
-            t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc, t.mpad, (double2*)t.part.p, t.ntiles,
-            nunits, (int*)c->d_err.p, 0, t.mpad, 0, nullptr);
+        launch_herm(c, t, g, t.kbpc, nunits, nullptr);
         ++nherm;
       }
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
@@ -902,7 +1207,8 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
                                                                            t.ntiles_f, nT, ng, out, accumulate);
       else
         k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks, t.ntiles,
-                                                                      ng, out, accumulate);
+                                                                      ng, out, accumulate, t.wide, t.nI,
+                                                                      t.tile_elems);
       int nk = 1;
       if (bg) {
         launch_bg_apply(bg->P + (size_t)jb.v * bg->nd, bg->didx, ng, bg->nd, 1, out, c->st, 0);
@@ -919,19 +1225,21 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       }
     }
   }
-  const double tile_bytes = (double)(kBM / 2) * (kBN / 2) * 16;
+  const double tile_bytes = (double)t.tile_elems * 16;
+  const double tile_bytes_f = (double)(kBM / 2) * (kBN / 2) * 16;
   // operand split: R read once per pass, hi/lo written (B once, A per job)
   c->stage[CHI0_STAGE_WEIGHTS].bytes +=
       (double)(passes + 1) * nt * ng * 8 + (double)(jobs.size() + 1) * 4.0 * t.mpad * t.kpad;
   // contraction: each launch streams A and B (hi and lo) once and writes its chunk partials
   c->stage[CHI0_STAGE_CONTRACT].bytes =
       (double)(nherm + nfull) * 8.0 * t.mpad * t.kpad +
-      ((double)nherm * t.nchunks * t.ntiles + (double)nfull * t.nchunks_f * t.ntiles_f) * tile_bytes;
+      (double)nherm * t.nchunks * t.ntiles * tile_bytes + (double)nfull * t.nchunks_f * t.ntiles_f * tile_bytes_f;
   c->stage[CHI0_STAGE_REDUCE].bytes =
-      ((double)nherm * t.nchunks * t.ntiles + (double)nfull * t.nchunks_f * t.ntiles_f) * tile_bytes +
+      (double)nherm * t.nchunks * t.ntiles * tile_bytes + (double)nfull * t.nchunks_f * t.ntiles_f * tile_bytes_f +
       (double)(nherm + nfull) * n2 * 16;
   // tensor-core work actually issued: 3 BF16 products over the tiles of each launch
-  c->tc_issued_flops = 3.0 * 2.0 * kBM * kBN * (double)t.kpad * ((double)t.ntiles * nherm + (double)t.ntiles_f * nfull);
+  c->tc_issued_flops = 3.0 * 2.0 * kBM * (double)t.kpad *
+                      ((double)(t.wide ? kWN : kBN) * t.ntiles * nherm + (double)kBN * t.ntiles_f * nfull);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
@@ -982,7 +1290,7 @@ chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
   oa.lo[0] = (__nv_bfloat16*)t.al[0].p;
   oa.wr[0] = (const double*)c->d_w.p;
   k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, oa, nullptr);
-  const size_t cap = t.part.bytes / ((size_t)(kBM / 2) * (kBN / 2) * 16);
+  const size_t cap = t.part.bytes / ((size_t)t.tile_elems * 16);
   const int base_split = (t.total_kb + t.kbpc - 1) / t.kbpc;
   int best_kbpc = t.kbpc, best_n = t.nchunks;
   float best = 1e30f;
@@ -1000,9 +1308,8 @@ chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {   // the first run warms the caches
       cudaEventRecord(e0, c->st);
-      k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[0], t.m_al[0], t.m_bh, t.m_bl, t.total_kb, kbpc,
-                                                            t.mpad, (double2*)t.part.p, t.ntiles, nunits,
-                                                            (int*)c->d_err.p, 0, t.mpad, 0, nullptr);
+      launch_herm(c, t, 0, kbpc, nunits, nullptr);
+      (void)grid;
       cudaEventRecord(e1, c->st);
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
         cudaGetLastError();
