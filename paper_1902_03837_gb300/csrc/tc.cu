@@ -31,6 +31,10 @@
 // Every mbarrier wait is bounded: on timeout the kernel raises the device
 // error flag (reported as CHI0_ETIMEOUT), skips the remaining work, frees its
 // TMEM and returns.
+// The Hermitian contraction (real weights) runs the wide variant of this
+// kernel, k_herk_wide: 128 x 256 tiles, N = 256 products, twelve warps (see
+// its comment); the full tile grid (complex weights of a real frequency, the
+// self-energy product) keeps the 128 x 128 kernel.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
