@@ -437,6 +437,39 @@ static double pole_weight_host(int kind, double om, double eta, double d) {
   return kind == 1 ? a / da - b / db : eta / db - eta / da;
 }
 
+// Sign shared by every imaginary-axis transition weight (the kind-0 weights of
+// k_weights).  pref (f_m - f_n) 2d/(d^2 + s^2) has the sign of its pole d at
+// every frequency (pref > 0, f_m - f_n > tol), and the extrapolar term
+// -pref f_m 2dbar/(dbar^2 + s^2) the sign of -dbar.  Returns -1 or +1 when no
+// nonzero term has the other sign, 0 when they are mixed or when a dense grid
+// makes the factor a mean over poles that are not known here.  dpole: the
+// pole energy each transition uses (its group representative's), or NULL for
+// its own.
+static int weight_sign(const chi0_ctx* c, const std::vector<double>* dpole) {
+  if (c->dg_nd > 0) return 0;
+  bool pos = false, neg = false;
+  const int nb = c->nb;
+  for (int64_t t = 0; t < c->nt; ++t) {
+    const int m = (int)(t % c->Nm);
+    const int64_t r = t / c->Nm;
+    const int n = c->n_lo + (int)(r % c->Nn);
+    const int ik = (int)(r / c->Nn), ikp = c->h_kq[ik];
+    const double fm = c->h_occ[(size_t)ikp * nb + m];
+    if (fm - c->h_occ[(size_t)ik * nb + n] > c->cfg.occ_drop_tol) {
+      const double d = dpole ? (*dpole)[t] : c->h_eps[(size_t)ikp * nb + m] - c->h_eps[(size_t)ik * nb + n];
+      pos |= d > 0.0;
+      neg |= d < 0.0;
+    }
+    if (c->bg_on && fm > c->cfg.occ_drop_tol) {
+      const double dbar = c->h_eps[(size_t)ikp * nb + m] - c->bg_eps;
+      pos |= dbar < 0.0;
+      neg |= dbar > 0.0;
+    }
+    if (pos && neg) return 0;
+  }
+  return neg ? -1 : 1;
+}
+
 // ---- Bruneval-Gonze extrapolar correction: planning and launch
 // Difference vectors d = G_i - G_j of the response set, ordered by (y, z, x)
 // (the order the rho kernel visits its G set in), cut into chunks of at most
@@ -670,6 +703,7 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
       } while (j < order.size() && d[order[j]] - dr < c->grp_thresh);
       i = j;
     }
+    c->herk_sign = weight_sign(c, &dp);
     chi0_status s0 = ensure(c, c->d_dpole, (size_t)nt * 8, "pole energies");
     if (s0 != CHI0_OK) return s0;
     CK(cudaMemcpyAsync(c->d_dpole.p, dp.data(), (size_t)nt * 8, cudaMemcpyHostToDevice, c->st), "poles H2D");
@@ -729,6 +763,7 @@ chi0_status plan_chi0(chi0_ctx* c, int iq) {
   } else {
     c->grouped = false;
     c->ngroups = 0;
+    c->herk_sign = weight_sign(c, nullptr);
   }
   if (c->nt > 0) {
     // transitions per contraction: all of them, or one band block's

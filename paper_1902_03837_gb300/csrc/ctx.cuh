@@ -110,6 +110,11 @@ struct chi0_ctx {
   DevBuf d_grange;                     // [ngroups] int2 (first k-block, k-blocks) of each group
   DevBuf d_ga;                         // [nt] double pref (f_m - f_n)
   DevBuf d_gfac;                       // [nwv][ngroups] float F_g(w) of the representatives
+  // sign shared by every transition weight of the imaginary-axis frequencies
+  // (-1: all <= 0, +1: all >= 0, 0: mixed or not known); nonzero lets the
+  // Hermitian contraction take the one-operand form chi0 = sign S S^H with
+  // S = rho diag(sqrt|w|)
+  int herk_sign = 0;
   int dg_nd = 0;                       // dense points per k; 0: off
   DevBuf d_epsd;                       // [nk][dg_nd][nb] dense-grid energies
   // self-energy kernel I (sigma.cu; its tensor-core operands in tc.cu):

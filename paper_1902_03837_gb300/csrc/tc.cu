@@ -9,6 +9,13 @@
 //     A[m][t] = P_t(i).c,   B[m][t] = rho_t(i).c,   D = A B^T  (2 N_G x 2 N_G),
 //     Re chi_ij = D[2i][2j] + D[2i+1][2j+1],   Im chi_ij = D[2i+1][2j] - D[2i][2j+1].
 //
+// When every weight has one sign s (on the imaginary axis w_t has the sign of
+// the pole, the same for all transitions unless occupations and energies are
+// out of order or an extrapolar term is added), the Hermitian contraction
+// takes the one-operand form chi0 = s S S^H with S_t = sqrt|w_t| rho_t: A and
+// B are both S (one operand set per frequency, half the bytes the tiles
+// stream), and the sign is applied when the partials are summed.
+//
 // Precision: each FP32 operand is split into two BF16 numbers, x = hi + lo
 // (hi = bf16(x), lo = bf16(x - hi), together ~16 bits), and
 // D = Ah Bh + Ah Bl + Al Bh (the lo*lo term, <= 2^-16 of a product, is
@@ -691,15 +698,18 @@ constexpr int kPI = 32;  // complex G per tile
 
 // Up to kPrepGroup operands are split in one pass, so that R is read once
 // for all of them (the split is bound by HBM traffic: R in, hi/lo out).
-// Operand g is R scaled by the weights wr[g][t] (NULL: unit weights), or, with
-// wi[g] given, by the complex weights wr[g][t] + i wi[g][t] (a real-axis
-// frequency: A = w rho with rows Re = wr x - wi y, Im = wr y + wi x).
+// Operand g is R scaled by the weights wr[g][t] (NULL: unit weights), by
+// sqrt|wr[g][t]| when sq[g] is set (the one-operand form S = rho diag(sqrt|w|)
+// of a contraction whose weights share one sign), or, with wi[g] given, by the
+// complex weights wr[g][t] + i wi[g][t] (a real-axis frequency: A = w rho with
+// rows Re = wr x - wi y, Im = wr y + wi x).
 constexpr int kPrepGroup = 8;
 struct PrepOut {
   __nv_bfloat16* hi[kPrepGroup];
   __nv_bfloat16* lo[kPrepGroup];
   const double* wr[kPrepGroup];
   const double* wi[kPrepGroup];
+  int sq[kPrepGroup];
 };
 
 // perm (optional): row t of the operand is transition perm[t] of R (-1: a
@@ -722,7 +732,12 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
   for (int e = threadIdx.x; e < ngrp * kPT; e += 256) {
     const int g = e / kPT, tl = e % kPT;
     const int64_t t = src[tl];
-    ws[g][tl] = (out.wr[g] && t >= 0) ? (float)out.wr[g][t] : 1.f;
+    if (out.wr[g] && t >= 0) {
+      const double wv = out.wr[g][t];
+      ws[g][tl] = (float)(out.sq[g] ? sqrt(fabs(wv)) : wv);
+    } else {
+      ws[g][tl] = 1.f;
+    }
     wsi[g][tl] = (out.wi[g] && t >= 0) ? (float)out.wi[g][t] : 0.f;
   }
   for (int e = threadIdx.x; e < kPT * kPI; e += 256) {
@@ -784,7 +799,8 @@ __device__ __forceinline__ void herm_pos(int i, int j, int wide, int nI, int& ti
 }
 
 __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int ntiles, int ng,
-                            double2* __restrict__ chi, int accumulate, int wide, int nI, int tile_elems) {
+                            double2* __restrict__ chi, int accumulate, int wide, int nI, int tile_elems,
+                            double sign) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
   const int i = (int)(e / ng), j = (int)(e % ng);
@@ -799,6 +815,8 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
     sy += v.y;
   }
   if (i == j) sy = 0.0;  // Hermitian: real diagonal
+  sx *= sign;            // the one-operand form sums sign S S^H
+  sy *= sign;
   if (accumulate) {      // add to the sum of the earlier transition blocks
     const double2 a = chi[(size_t)i * ng + j];
     sx += a.x;
@@ -858,17 +876,21 @@ void herm_tiles(TcState& t) {
   }
 }
 
-// One Hermitian contraction launch (lower-triangle tiles x transition splits)
-cudaError_t launch_herm(chi0_ctx* c, TcState& t, int g, int kbpc, int nunits, const int2* ranges) {
+// One Hermitian contraction launch (lower-triangle tiles x transition splits).
+// one_op: the one-operand form D = S S^T, both tiles read from operand g;
+// otherwise A is operand g and B the unit-weight operand.
+cudaError_t launch_herm(chi0_ctx* c, TcState& t, int g, int kbpc, int nunits, const int2* ranges, bool one_op) {
   const unsigned grid = (unsigned)std::min(nunits, std::max(1, t.nsm));
+  const CUtensorMap& mbh = one_op ? t.m_ah[g] : t.m_bh;
+  const CUtensorMap& mbl = one_op ? t.m_al[g] : t.m_bl;
   if (t.wide)
-    k_herk_wide<<<grid, kWThreads, kWSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, kbpc,
-                                                          t.mpad, (double2*)t.part.p, t.ntiles, nunits,
-                                                          (int*)c->d_err.p, t.nI, ranges);
+    k_herk_wide<<<grid, kWThreads, kWSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], mbh, mbl, t.total_kb, kbpc, t.mpad,
+                                                          (double2*)t.part.p, t.ntiles, nunits, (int*)c->d_err.p,
+                                                          t.nI, ranges);
   else
-    k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, kbpc,
-                                                          t.mpad, (double2*)t.part.p, t.ntiles, nunits,
-                                                          (int*)c->d_err.p, 0, t.mpad, 0, ranges);
+    k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], mbh, mbl, t.total_kb, kbpc, t.mpad,
+                                                          (double2*)t.part.p, t.ntiles, nunits, (int*)c->d_err.p, 0,
+                                                          t.mpad, 0, ranges);
   return cudaGetLastError();
 }
 
@@ -1097,21 +1119,21 @@ chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_f
   const int64_t n2 = (int64_t)ng * ng;
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
   const int64_t* perm = (const int64_t*)c->d_tperm.p;
-  // operands in group order: B = rho, A = pref (f_m - f_n) rho (frequency independent)
-  PrepOut ob{}, oa{};
-  ob.hi[0] = (__nv_bfloat16*)t.bh.p;
-  ob.lo[0] = (__nv_bfloat16*)t.bl.p;
+  // one operand in group order, S = rho diag(sqrt(pref (f_m - f_n))) (frequency
+  // independent; every grouped transition has f_m - f_n > 0), so that the
+  // group sums are M_g = S_g S_g^H
+  PrepOut oa{};
   oa.hi[0] = (__nv_bfloat16*)t.ah[0].p;
   oa.lo[0] = (__nv_bfloat16*)t.al[0].p;
   oa.wr[0] = (const double*)c->d_ga.p;
+  oa.sq[0] = 1;
   stage_begin(c, CHI0_STAGE_WEIGHTS);
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, t.kpad, ng, t.mpad, ob, perm);
   k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, t.kpad, ng, t.mpad, oa, perm);
-  stage_end(c, CHI0_STAGE_WEIGHTS, 2);
+  stage_end(c, CHI0_STAGE_WEIGHTS, 1);
   // one unit per (tile, group): the group sums M_g, tile by tile
   const int nunits = t.ntiles * c->ngroups;
   stage_begin(c, CHI0_STAGE_CONTRACT);
-  launch_herm(c, t, 0, t.total_kb, nunits, (const int2*)c->d_grange.p);
+  launch_herm(c, t, 0, t.total_kb, nunits, (const int2*)c->d_grange.p, true);
   stage_end(c, CHI0_STAGE_CONTRACT, 1);
   // chi0 at every frequency from the group sums and the groups' factors
   const unsigned cgrid = (unsigned)((n2 + 255) / 256);
@@ -1126,8 +1148,8 @@ chi0_status tc_launch_grouped(chi0_ctx* c, double2* chi, const cudaEvent_t* ev_f
   }
   stage_end(c, CHI0_STAGE_REDUCE, nlaunch);
   const double tile_bytes = (double)t.tile_elems * 16;
-  c->stage[CHI0_STAGE_WEIGHTS].bytes = 2.0 * (double)c->nt * ng * 8 + 2.0 * 4.0 * t.mpad * t.kpad;
-  c->stage[CHI0_STAGE_CONTRACT].bytes = 8.0 * t.mpad * t.kpad + (double)nunits * tile_bytes;
+  c->stage[CHI0_STAGE_WEIGHTS].bytes = (double)c->nt * ng * 8 + 4.0 * t.mpad * t.kpad;
+  c->stage[CHI0_STAGE_CONTRACT].bytes = 4.0 * t.mpad * t.kpad + (double)nunits * tile_bytes;
   // the work done: one Hermitian contraction over the transitions in group
   // order (not one per frequency), then the combination per frequency
   c->stage[CHI0_STAGE_CONTRACT].flops = 4.0 * (double)ng * (ng + 1) * (double)t.kpad;
@@ -1147,13 +1169,6 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
   const int64_t n2 = (int64_t)ng * ng;
   const int nT = t.mpad / kBM;
-  // B = rho (frequency independent)
-  PrepOut ob{};
-  ob.hi[0] = (__nv_bfloat16*)t.bh.p;
-  ob.lo[0] = (__nv_bfloat16*)t.bl.p;
-  stage_begin(c, CHI0_STAGE_WEIGHTS);
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, 1, nt, ng, t.mpad, ob, nullptr);
-  stage_end(c, CHI0_STAGE_WEIGHTS, 1);
   // jobs: an entry of the frequency list with real weights is one Hermitian
   // contraction (lower-triangle tiles); a real-axis frequency (entries of
   // kinds 1 and 2: the real and imaginary parts of its complex weights) is one
@@ -1169,6 +1184,21 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
     jobs.push_back({v, cplx});
     if (cplx) ++v;
   }
+  // A Hermitian job whose weights share one sign takes the one-operand form
+  // chi0 = sign S S^H with S = rho diag(sqrt|w|): one operand set per
+  // frequency, read for both tiles.  Otherwise (mixed signs) A = w rho and
+  // B = rho; the complex jobs also read B.
+  const bool one_op = c->herk_sign != 0;
+  bool need_b = !one_op;
+  for (const Job& jb : jobs) need_b |= jb.cplx;
+  if (need_b) {   // B = rho (frequency independent)
+    PrepOut ob{};
+    ob.hi[0] = (__nv_bfloat16*)t.bh.p;
+    ob.lo[0] = (__nv_bfloat16*)t.bl.p;
+    stage_begin(c, CHI0_STAGE_WEIGHTS);
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, 1, nt, ng, t.mpad, ob, nullptr);
+    stage_end(c, CHI0_STAGE_WEIGHTS, 1);
+  }
   const int nunits = t.ntiles * t.nchunks, nunits_f = t.ntiles_f * t.nchunks_f;
   const unsigned hgrid = (unsigned)std::min(nunits, std::max(1, t.nsm));
   const unsigned hgrid_f = (unsigned)std::min(nunits_f, std::max(1, t.nsm));
@@ -1182,6 +1212,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       oa.lo[g] = (__nv_bfloat16*)t.al[g].p;
       oa.wr[g] = w + (size_t)jb.v * nt;
       oa.wi[g] = jb.cplx ? w + (size_t)(jb.v + 1) * nt : nullptr;
+      oa.sq[g] = one_op && !jb.cplx;
     }
     stage_begin(c, CHI0_STAGE_WEIGHTS);
     k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)R, gw, nt, ng, t.mpad, oa, nullptr);
@@ -1201,7 +1232,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
             nunits_f, (int*)c->d_err.p, nT, t.mpad, 0, nullptr);
         ++nfull;
       } else {
-        launch_herm(c, t, g, t.kbpc, nunits, nullptr);
+        launch_herm(c, t, g, t.kbpc, nunits, nullptr, one_op);
         ++nherm;
       }
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
@@ -1212,7 +1243,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       else
         k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks, t.ntiles,
                                                                       ng, out, accumulate, t.wide, t.nI,
-                                                                      t.tile_elems);
+                                                                      t.tile_elems, one_op ? (double)c->herk_sign : 1.0);
       int nk = 1;
       if (bg) {
         launch_bg_apply(bg->P + (size_t)jb.v * bg->nd, bg->didx, ng, bg->nd, 1, out, c->st, 0);
@@ -1231,12 +1262,13 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
   }
   const double tile_bytes = (double)t.tile_elems * 16;
   const double tile_bytes_f = (double)(kBM / 2) * (kBN / 2) * 16;
-  // operand split: R read once per pass, hi/lo written (B once, A per job)
-  c->stage[CHI0_STAGE_WEIGHTS].bytes +=
-      (double)(passes + 1) * nt * ng * 8 + (double)(jobs.size() + 1) * 4.0 * t.mpad * t.kpad;
-  // contraction: each launch streams A and B (hi and lo) once and writes its chunk partials
+  // operand split: R read once per pass, hi/lo written (B once if needed, A per job)
+  c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(passes + (need_b ? 1 : 0)) * nt * ng * 8 +
+                                        (double)(jobs.size() + (need_b ? 1 : 0)) * 4.0 * t.mpad * t.kpad;
+  // contraction: each launch streams its operands (hi and lo) once, one set
+  // in the one-operand form and two otherwise, and writes its chunk partials
   c->stage[CHI0_STAGE_CONTRACT].bytes =
-      (double)(nherm + nfull) * 8.0 * t.mpad * t.kpad +
+      (double)nherm * (one_op ? 4.0 : 8.0) * t.mpad * t.kpad + (double)nfull * 8.0 * t.mpad * t.kpad +
       (double)nherm * t.nchunks * t.ntiles * tile_bytes + (double)nfull * t.nchunks_f * t.ntiles_f * tile_bytes_f;
   c->stage[CHI0_STAGE_REDUCE].bytes =
       (double)nherm * t.nchunks * t.ntiles * tile_bytes + (double)nfull * t.nchunks_f * t.ntiles_f * tile_bytes_f +
@@ -1285,14 +1317,18 @@ chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
   TcState& t = *static_cast<TcState*>(c->tc);
   const int ng = c->cfg.ng;
   const dim3 pgrid((unsigned)(t.kpad / kPT), (unsigned)(t.mpad / 2 / kPI));
-  PrepOut ob{};
-  ob.hi[0] = (__nv_bfloat16*)t.bh.p;
-  ob.lo[0] = (__nv_bfloat16*)t.bl.p;
-  k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, ob, nullptr);
+  const bool one_op = c->herk_sign != 0;
+  if (!one_op) {
+    PrepOut ob{};
+    ob.hi[0] = (__nv_bfloat16*)t.bh.p;
+    ob.lo[0] = (__nv_bfloat16*)t.bl.p;
+    k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, ob, nullptr);
+  }
   PrepOut oa{};
   oa.hi[0] = (__nv_bfloat16*)t.ah[0].p;
   oa.lo[0] = (__nv_bfloat16*)t.al[0].p;
   oa.wr[0] = (const double*)c->d_w.p;
+  oa.sq[0] = one_op;
   k_prep<<<pgrid, 256, 0, c->st>>>((const float2*)c->d_R.p, 1, c->nt, ng, t.mpad, oa, nullptr);
   const size_t cap = t.part.bytes / ((size_t)t.tile_elems * 16);
   const int base_split = (t.total_kb + t.kbpc - 1) / t.kbpc;
@@ -1312,7 +1348,7 @@ chi0_status tc_tune_split(chi0_ctx* c, float* best_ms) {
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {   // the first run warms the caches
       cudaEventRecord(e0, c->st);
-      launch_herm(c, t, 0, kbpc, nunits, nullptr);
+      launch_herm(c, t, 0, kbpc, nunits, nullptr, one_op);
       (void)grid;
       cudaEventRecord(e1, c->st);
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {

@@ -79,6 +79,49 @@ def test_mixed_small(lib, case):
     assert np.abs(got["chi"] - np.conj(np.transpose(got["chi"], (0, 2, 1)))).max() == 0.0
 
 
+def _chi_only(lib, s):
+    import torch
+    ctx = lib.Chi0.for_system(s, precision=lib.CHI0_MIXED_BF16X3,
+                              stream=torch.cuda.current_stream().cuda_stream)
+    ctx.load_system(s)
+    ctx.compute_rho(0)
+    nt = ctx.get_transitions().shape[0]
+    chi = np.zeros((s.freqs.size, s.ng, s.ng), np.complex128)
+    ctx.build_chi0(0, chi)
+    ctx.synchronize()
+    _, by, _, _ = ctx.get_stats()
+    ctx.close()
+    return chi, by["contract"], nt
+
+
+def test_mixed_sign_weights(lib):
+    """Imaginary-axis weights of one sign take the one-operand form
+    chi0 = -S S^H with S = rho diag(sqrt|w|); weights of both signs (here: an
+    occupied band lifted above every empty one at one k - q point, so its
+    transitions get poles d = e_m - e_n > 0) take the two-operand form
+    A = w rho, B = rho, which streams twice the operand bytes.  Both against
+    the oracle."""
+    case = dict(kgrid=(2, 2, 2), q_frac=((0.5, 0.0, 0.0),), fft=(20, 20, 20), ng=45, n_occ=5,
+                n_bands=23, npw_target=90, a=8.0, freqs=(0.05j, 0.4j, 3.0j), eta=0.0)
+    s = make_system(cfg_tiny(seed=43, coef_dtype="c64", **case))
+    G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
+    chi1, by1, nt = _chi_only(lib, s)
+    e1 = _rel(chi1, O.chi0_tr(s, 0, G, s.freqs, s.eta))
+    assert e1 < TOL, e1
+    s.eps[3, 4] = s.eps.max() + 0.1
+    w = O.weights_tr(s, 0, O.transitions_tr(s, 0), s.freqs, s.eta).real
+    assert (w > 0).any() and (w < 0).any()
+    chi2, by2, nt2 = _chi_only(lib, s)
+    e2 = _rel(chi2, O.chi0_tr(s, 0, G, s.freqs, s.eta))
+    assert e2 < TOL, e2
+    # the two forms differ in the operand bytes the contraction streams:
+    # 4 bytes (hi and lo BF16) per real row and transition for each extra operand
+    assert nt2 == nt
+    mpad = (2 * s.ng + 255) // 256 * 256
+    kpad = (nt + 63) // 64 * 64
+    assert by2 - by1 == s.freqs.size * 4.0 * mpad * kpad, (by1, by2)
+
+
 @pytest.mark.slow
 def test_precision_workload_full_size(lib):
     """8x8x8 k, 16+184 bands, ~2000 PW, FFT 48^3, N_G = 1000, 32 imaginary
