@@ -966,8 +966,13 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
   const size_t opb = (size_t)t.mpad * t.kpad * 2;
   chi0_status s;
-  if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
-  if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
+  // the unit-weight operand B is read only by the two-operand form (weights
+  // of mixed signs) and by the complex contractions of real frequencies
+  const bool need_b = c->herk_sign == 0 || c->has_real;
+  if (need_b) {
+    if ((s = ctx_ensure(c, t.bh, opb, "B hi")) != CHI0_OK) return s;
+    if ((s = ctx_ensure(c, t.bl, opb, "B lo")) != CHI0_OK) return s;
+  }
   // a batch problem (group_cap > 0) keeps room for twice the planned
   // partials, for the split candidates of tc_tune_split
   const size_t room = c->group_cap > 0 ? 2 : 1;
@@ -996,7 +1001,7 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
     if (!make_map(&t.m_ah[g], t.ah[g].p, t.kpad, t.mpad) || !make_map(&t.m_al[g], t.al[g].p, t.kpad, t.mpad))
       return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   }
-  if (!make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
+  if (need_b && (!make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad)))
     return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
@@ -1090,13 +1095,12 @@ chi0_status tc_plan_grouped(chi0_ctx* c, int ng, int nw) {
     return ctx_fail(c, CHI0_EUNSUPPORTED, "too many grouped transitions for one contraction");
   const size_t opb = (size_t)t.mpad * t.kpad * 2;
   chi0_status s;
-  DevBuf* ops[] = {&t.bh, &t.bl, &t.ah[0], &t.al[0]};
+  DevBuf* ops[] = {&t.ah[0], &t.al[0]};   // one operand (S S^H form)
   for (DevBuf* b : ops)
     if ((s = ctx_ensure(c, *b, opb, "grouped operands")) != CHI0_OK) return s;
   if ((s = ctx_ensure(c, t.part, (size_t)c->ngroups * t.ntiles * t.tile_elems * 16, "group sums")) != CHI0_OK)
     return s;
-  if (!make_map(&t.m_ah[0], t.ah[0].p, t.kpad, t.mpad) || !make_map(&t.m_al[0], t.al[0].p, t.kpad, t.mpad) ||
-      !make_map(&t.m_bh, t.bh.p, t.kpad, t.mpad) || !make_map(&t.m_bl, t.bl.p, t.kpad, t.mpad))
+  if (!make_map(&t.m_ah[0], t.ah[0].p, t.kpad, t.mpad) || !make_map(&t.m_al[0], t.al[0].p, t.kpad, t.mpad))
     return ctx_fail(c, CHI0_ECUDA, "cuTensorMapEncodeTiled failed");
   cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e == cudaSuccess)
