@@ -638,6 +638,8 @@ def run_ours(args, rank, world, dist):
         roofs.update({"contract": ("fp64", "TFLOP/s", "k_chi0_fp64"), "rho": ("fp64", "TFLOP/s", "k_rho_pairs"),
                       "wf_grid": ("fp64", "TFLOP/s", "k_wf_to_mixed")})
     bound, unit, kname = roofs[dom]
+    if dom == "contract" and args.real_axis:
+        kname = "k_herk_bf16x3"   # complex weights: every 128 x 128 tile
     extra = {}
     if unit == "GB/s":
         achieved = st_bytes[dom] / (per_step_ms[dom] * 1e-3) / 1e9
@@ -972,7 +974,7 @@ def run_large(args, rank, world, dist):
                    "l2": "inputs larger than L2", "warmup_note": "warm-up steps on a 2x2x2 k grid of the same shape",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "input_generation_s": gen_s, "stage_ms_per_step": per, "stage_roofline": stages,
-        "roofline": {"kernel": "k_herk_bf16x3", "stage": "contract", "bound": "tensor",
+        "roofline": {"kernel": "k_herk_wide", "stage": "contract", "bound": "tensor",
                      "achieved": con.get("tflops"), "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
                      "frac": con.get("tensor_frac"), "peak_source": f"BF16 dense sustained ({pk['source']})",
                      "traffic": None, "traffic_source": "not captured for this workload"},

@@ -1004,7 +1004,8 @@ chi0_status plan_eps(chi0_ctx* c, int iq, double2* A) {
     // gaps between contraction launches.
     CK(cudaStreamCreateWithPriority(&c->s_ct, cudaStreamNonBlocking, least), "pipeline stream");
     CK(cudaStreamCreateWithPriority(&c->s_dy, cudaStreamNonBlocking, greatest), "pipeline stream");
-    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join_ct, &c->ev_join_dy};
+    CK(cudaStreamCreateWithPriority(&c->s_dy2, cudaStreamNonBlocking, greatest), "pipeline stream");
+    cudaEvent_t* evs[] = {&c->ev_fork, &c->ev_join_ct, &c->ev_join_dy, &c->ev_join_dy2};
     for (cudaEvent_t* e : evs) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "pipeline event");
   }
   // one event per entry of the contraction's frequency list
@@ -1073,9 +1074,9 @@ chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
   cudaEventRecord(c->ev_fork, base);
   cudaStreamWaitEvent(c->s_ct, c->ev_fork, 0);
   cudaStreamWaitEvent(c->s_dy, c->ev_fork, 0);
+  cudaStreamWaitEvent(c->s_dy2, c->ev_fork, 0);
   c->st = c->s_ct;
   s = launch_chi0(c, c->ev_freq.data(), c->ev_prep.data(), /*defer_combine=*/true);
-  c->st = c->s_dy;
   // Dyson steps in groups of 4 frequencies: the pivot-block inverses of a
   // group run side by side (one SM each), which a single frequency's chain
   // of 32 dependent pivot steps cannot hide.  The last four frequencies go
@@ -1083,7 +1084,12 @@ chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
   // Dyson step is left.  A group holds frequencies of one kind (imaginary
   // axis: Hermitian eps~; real axis: general eps~, whose chi0 is first
   // combined from its two contractions H_r + i H_i).
+  // Consecutive groups alternate between two Dyson streams, each with its
+  // own panel scratch (the group's slice of the per-frequency buffers), so
+  // that the pivot-block inverses of one group (one SM per matrix) overlap
+  // the rank-32 updates of the other.
   const int nT = (ng + 31) / 32;
+  int grp = 0;
   auto general = [&](int iw) { return c->has_real && c->h_vi[iw] >= 0; };
   auto first_v = [&](int iw) { return c->has_real ? c->h_vr[iw] : iw; };   // list entries of frequency iw
   auto last_v = [&](int iw) { return general(iw) ? c->h_vi[iw] : first_v(iw); };
@@ -1095,16 +1101,17 @@ chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
         gw = g;
         break;
       }
-    cudaStreamWaitEvent(c->s_dy, c->ev_freq[last_v(w0 + gw - 1)], 0);
+    c->st = (grp++ & 1) ? c->s_dy2 : c->s_dy;
+    cudaStreamWaitEvent(c->st, c->ev_freq[last_v(w0 + gw - 1)], 0);
     // and, when a split pass follows, until it is done: the Dyson blocks then
     // share the SMs with the (tensor-bound) contraction, not with the
     // (bandwidth-bound) split
-    if (w0 + gw < nw) cudaStreamWaitEvent(c->s_dy, c->ev_prep[first_v(w0 + gw)], 0);
+    if (w0 + gw < nw) cudaStreamWaitEvent(c->st, c->ev_prep[first_v(w0 + gw)], 0);
     cudaError_t e = cudaSuccess;
     if (c->has_real) {
       chi0::stage_begin(c, CHI0_STAGE_REDUCE);
       e = chi0::launch_combine_freq((const double2*)c->d_chiv.p, (const int*)c->d_vr.p + w0,
-                                    (const int*)c->d_vi.p + w0, ng, gw, (double2*)c->d_chi.p + w0 * n2, c->s_dy);
+                                    (const int*)c->d_vi.p + w0, ng, gw, (double2*)c->d_chi.p + w0 * n2, c->st);
       chi0::stage_end(c, CHI0_STAGE_REDUCE, 1);
       if (e != cudaSuccess) s = cuda_fail(c, e, "frequency combine launch");
     }
@@ -1112,19 +1119,20 @@ chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
     chi0::stage_begin(c, CHI0_STAGE_DYSON);
     const double2* chi = (const double2*)c->d_chi.p + w0 * n2;
     double2* out = c->plan_eps_out + w0 * n2;
-    e = general(w0) ? chi0::launch_dyson_general(chi, (const double*)c->d_vsqrt.p, ng, gw, out,
-                                                 (double2*)c->d_colp.p, (double2*)c->d_rowp.p,
-                                                 (double2*)c->d_pinv.p, (int*)c->d_err.p, c->s_dy)
-                    : chi0::launch_dyson(chi, (const double*)c->d_vsqrt.p, ng, gw, out, (double2*)c->d_colp.p,
-                                         (double2*)c->d_rowp.p, (double2*)c->d_pinv.p, (int*)c->d_err.p,
-                                         c->s_dy);
+    double2* colp = (double2*)c->d_colp.p + (size_t)w0 * ng * 32;
+    double2* rowp = (double2*)c->d_rowp.p + (size_t)w0 * ng * 32;
+    double2* pinv = (double2*)c->d_pinv.p + (size_t)w0 * 32 * 32;
+    e = general(w0) ? chi0::launch_dyson_general(chi, (const double*)c->d_vsqrt.p, ng, gw, out, colp, rowp, pinv,
+                                                 (int*)c->d_err.p, c->st)
+                    : chi0::launch_dyson(chi, (const double*)c->d_vsqrt.p, ng, gw, out, colp, rowp, pinv,
+                                         (int*)c->d_err.p, c->st);
     if (e != cudaSuccess) s = cuda_fail(c, e, "dyson launch");
     chi0::stage_end(c, CHI0_STAGE_DYSON, (general(w0) ? 1 : 2) + 3 * nT);
     // a host output receives each group as soon as it is inverted, so that
     // only the last group's copy follows the last contraction
     if (s == CHI0_OK && host_out) {
       e = cudaMemcpyAsync((char*)host_out + (size_t)w0 * n2 * 16, out, (size_t)gw * n2 * 16,
-                          cudaMemcpyDeviceToHost, c->s_dy);
+                          cudaMemcpyDeviceToHost, c->st);
       if (e != cudaSuccess) s = cuda_fail(c, e, "eps copy out");
     }
     w0 += gw;
@@ -1133,8 +1141,10 @@ chi0_status launch_chi0_eps(chi0_ctx* c, void* host_out, bool* copied) {
   // join (also on failure, so that a capture stays well formed)
   cudaEventRecord(c->ev_join_ct, c->s_ct);
   cudaEventRecord(c->ev_join_dy, c->s_dy);
+  cudaEventRecord(c->ev_join_dy2, c->s_dy2);
   cudaStreamWaitEvent(base, c->ev_join_ct, 0);
   cudaStreamWaitEvent(base, c->ev_join_dy, 0);
+  cudaStreamWaitEvent(base, c->ev_join_dy2, 0);
   if (s != CHI0_OK) return s;
   c->stage[CHI0_STAGE_DYSON].flops = 8.0 * (double)ng * ng * ng * nw;
   c->stage[CHI0_STAGE_DYSON].bytes = 2.0 * (double)n2 * nw * 16;
@@ -1762,13 +1772,13 @@ void chi0_destroy(chi0_ctx* c) {
       if (e) cudaEventDestroy(e);
   chi0::tc_release(c);
   chi0::sig_tc_release(c);
-  cudaStream_t pst[] = {c->s_ct, c->s_dy};
+  cudaStream_t pst[] = {c->s_ct, c->s_dy, c->s_dy2};
   for (cudaStream_t t : pst)
     if (t) {
       cudaStreamSynchronize(t);
       cudaStreamDestroy(t);
     }
-  cudaEvent_t pev[] = {c->ev_fork, c->ev_join_ct, c->ev_join_dy};
+  cudaEvent_t pev[] = {c->ev_fork, c->ev_join_ct, c->ev_join_dy, c->ev_join_dy2};
   for (cudaEvent_t e : pev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_freq)

@@ -140,6 +140,8 @@ struct chi0_ctx {
   // s_ct (lowest priority), the Dyson steps of finished frequencies on s_dy
   // (highest priority), both forked from and joined back into st
   cudaStream_t s_ct = nullptr, s_dy = nullptr;
+  cudaStream_t s_dy2 = nullptr;      // second Dyson stream: consecutive groups alternate
+  cudaEvent_t ev_join_dy2 = nullptr;
   std::vector<cudaEvent_t> ev_freq;  // [nw] contraction (and reduction) of frequency w done
   std::vector<cudaEvent_t> ev_prep;  // [nw] operand split of frequency w done
   cudaEvent_t ev_fork = nullptr, ev_join_ct = nullptr, ev_join_dy = nullptr;
