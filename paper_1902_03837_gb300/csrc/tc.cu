@@ -19,7 +19,8 @@
 // Precision: each FP32 operand is split into two BF16 numbers, x = hi + lo
 // (hi = bf16(x), lo = bf16(x - hi), together ~16 bits), and
 // D = Ah Bh + Ah Bl + Al Bh (the lo*lo term, <= 2^-16 of a product, is
-// dropped).  The tensor core's FP32 accumulation loses low bits on every
+// dropped; in the one-operand form lo carries a correction that keeps the
+// diagonal free of that term's bias, see k_prep).  The tensor core's FP32 accumulation loses low bits on every
 // addition with a bias (measured: the error grows linearly with the number of
 // accumulated transitions, ~2e-6 relative per 512), so each TMEM accumulation
 // is limited to 128 transitions; the epilogue warps fold those sub-sums into
@@ -702,7 +703,11 @@ constexpr int kPI = 32;  // complex G per tile
 // sqrt|wr[g][t]| when sq[g] is set (the one-operand form S = rho diag(sqrt|w|)
 // of a contraction whose weights share one sign), or, with wi[g] given, by the
 // complex weights wr[g][t] + i wi[g][t] (a real-axis frequency: A = w rho with
-// rows Re = wr x - wi y, Im = wr y + wi x).
+// rows Re = wr x - wi y, Im = wr y + wi x).  In the one-operand form the
+// dropped lo lo^T is a sum of squares on the diagonal (a bias of about
+// -2.8e-6 relative on every chi0_ii, where the two-operand form's dropped
+// terms have no sign); the split then stores lo' = lo + lo^2 / (2 hi) in
+// place of lo, which makes the diagonal's products hi^2 + 2 hi lo' = x^2.
 constexpr int kPrepGroup = 8;
 struct PrepOut {
   __nv_bfloat16* hi[kPrepGroup];
@@ -774,7 +779,16 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
         x1 = tile[ml][2 * tp + 1] * ws[g][2 * tp + 1];
       }
       const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-      const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+      const float h0 = __low2float(h), h1 = __high2float(h);
+      float r0 = x0 - h0, r1 = x1 - h1;   // exact
+      if (out.sq[g]) {
+        // one-operand form: lo' = lo + lo^2 / (2 hi), so that the products
+        // taken, hi^2 + 2 hi lo', equal x^2 up to the (unbiased) rounding of
+        // lo'; otherwise the dropped lo^2 would bias every diagonal entry
+        r0 = fmaf(r0 * r0, h0 != 0.f ? __fdividef(0.5f, h0) : 0.f, r0);
+        r1 = fmaf(r1 * r1, h1 != 0.f ? __fdividef(0.5f, h1) : 0.f, r1);
+      }
+      const __nv_bfloat162 l = __floats2bfloat162_rn(r0, r1);
       const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
       *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
       *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
