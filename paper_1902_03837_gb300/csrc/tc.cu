@@ -739,7 +739,9 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
     const int64_t t = src[tl];
     if (out.wr[g] && t >= 0) {
       const double wv = out.wr[g][t];
-      ws[g][tl] = (float)(out.sq[g] ? sqrt(fabs(wv)) : wv);
+      // sqrt|w| in FP32 (2^-24 relative, far below the split's 2^-17; the
+      // FP64 square root is slow on this part)
+      ws[g][tl] = out.sq[g] ? sqrtf(fabsf((float)wv)) : (float)wv;
     } else {
       ws[g][tl] = 1.f;
     }

@@ -106,8 +106,14 @@ def test_mixed_sign_weights(lib):
     s = make_system(cfg_tiny(seed=43, coef_dtype="c64", **case))
     G = O.response_gvectors(s.spec.kgrid, s.q_frac[0], s.ng)
     chi1, by1, nt = _chi_only(lib, s)
-    e1 = _rel(chi1, O.chi0_tr(s, 0, G, s.freqs, s.eta))
+    ref1 = O.chi0_tr(s, 0, G, s.freqs, s.eta)
+    e1 = _rel(chi1, ref1)
     assert e1 < TOL, e1
+    # the one-operand split keeps the diagonal unbiased: without the lo'
+    # correction every chi0_ii is low by about 3e-6 relative (sum of lo^2)
+    for w in range(s.freqs.size):
+        d = np.diagonal(chi1[w] - ref1[w]).real / np.diagonal(ref1[w]).real
+        assert abs(d.mean()) < 1.5e-6, (w, d.mean())
     s.eps[3, 4] = s.eps.max() + 0.1
     w = O.weights_tr(s, 0, O.transitions_tr(s, 0), s.freqs, s.eta).real
     assert (w > 0).any() and (w < 0).any()
