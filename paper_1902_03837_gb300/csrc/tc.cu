@@ -725,6 +725,7 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
   __shared__ float tile[2 * kPI][kPT + 1];
   __shared__ float ws[kPrepGroup][kPT];   // weights converted once per transition (FP64 is slow here)
   __shared__ float wsi[kPrepGroup][kPT];  // imaginary parts of complex weights
+  __shared__ float rs[kPrepGroup][kPT];   // one-operand form: 0.5 / sqrt|w| (0 for w = 0)
   __shared__ int64_t src[kPT];            // transition of each row (-1: zero row)
   const int64_t kb = blockIdx.x;
   const int64_t t0 = kb * kPT;
@@ -741,9 +742,12 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
       const double wv = out.wr[g][t];
       // sqrt|w| in FP32 (2^-24 relative, far below the split's 2^-17; the
       // FP64 square root is slow on this part)
-      ws[g][tl] = out.sq[g] ? sqrtf(fabsf((float)wv)) : (float)wv;
+      const float sw = sqrtf(fabsf((float)wv));
+      ws[g][tl] = out.sq[g] ? sw : (float)wv;
+      rs[g][tl] = sw > 0.f ? 0.5f / sw : 0.f;
     } else {
       ws[g][tl] = 1.f;
+      rs[g][tl] = 0.f;
     }
     wsi[g][tl] = (out.wi[g] && t >= 0) ? (float)out.wi[g][t] : 0.f;
   }
@@ -757,14 +761,17 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
   }
   __syncthreads();
   const size_t blk = (size_t)kb * mpad * kPT;
-  for (int g = 0; g < ngrp; ++g) {
-    __nv_bfloat16* __restrict__ hi = out.hi[g];
-    __nv_bfloat16* __restrict__ lo = out.lo[g];
-    const bool cplx = out.wi[g] != nullptr;
-    for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
-      const int ml = e / (kPT / 2), tp = e % (kPT / 2);
+  // every element pair once, through all operands of the pass: the R values
+  // and their reciprocals (for the one-operand correction) are shared
+  for (int e = threadIdx.x; e < 2 * kPI * (kPT / 2); e += 256) {
+    const int ml = e / (kPT / 2), tp = e % (kPT / 2);
+    const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
+    const float y0 = tile[ml][2 * tp], y1 = tile[ml][2 * tp + 1];
+    const float ry0 = y0 != 0.f ? __fdividef(1.f, y0) : 0.f;
+    const float ry1 = y1 != 0.f ? __fdividef(1.f, y1) : 0.f;
+    for (int g = 0; g < ngrp; ++g) {
       float x0, x1;
-      if (cplx) {
+      if (out.wi[g]) {
         // row 2 i: Re(w rho) = wr x - wi y; row 2 i + 1: Im(w rho) = wr y + wi x
         const int mr = ml & ~1;
         const float a0 = tile[mr][2 * tp], b0 = tile[mr + 1][2 * tp];
@@ -777,23 +784,23 @@ k_prep(const float2* __restrict__ R, int ngrp, int64_t nt, int ng, int mpad, con
           x1 = fmaf(ws[g][2 * tp + 1], a1, -wsi[g][2 * tp + 1] * b1);
         }
       } else {
-        x0 = tile[ml][2 * tp] * ws[g][2 * tp];
-        x1 = tile[ml][2 * tp + 1] * ws[g][2 * tp + 1];
+        x0 = y0 * ws[g][2 * tp];
+        x1 = y1 * ws[g][2 * tp + 1];
       }
       const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-      const float h0 = __low2float(h), h1 = __high2float(h);
-      float r0 = x0 - h0, r1 = x1 - h1;   // exact
+      float r0 = x0 - __low2float(h), r1 = x1 - __high2float(h);   // exact
       if (out.sq[g]) {
         // one-operand form: lo' = lo + lo^2 / (2 hi), so that the products
         // taken, hi^2 + 2 hi lo', equal x^2 up to the (unbiased) rounding of
-        // lo'; otherwise the dropped lo^2 would bias every diagonal entry
-        r0 = fmaf(r0 * r0, h0 != 0.f ? __fdividef(0.5f, h0) : 0.f, r0);
-        r1 = fmaf(r1 * r1, h1 != 0.f ? __fdividef(0.5f, h1) : 0.f, r1);
+        // lo'; otherwise the dropped lo^2 would bias every diagonal entry.
+        // 1 / (2 x) = (1 / R) (0.5 / sqrt|w|) stands in for 1 / (2 hi): they
+        // differ by 2^-9 relative, far below what the correction needs
+        r0 = fmaf(r0 * r0, ry0 * rs[g][2 * tp], r0);
+        r1 = fmaf(r1 * r1, ry1 * rs[g][2 * tp + 1], r1);
       }
       const __nv_bfloat162 l = __floats2bfloat162_rn(r0, r1);
-      const size_t off = blk + (size_t)(2 * i0 + ml) * kPT + 2 * tp;
-      *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
-      *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+      *reinterpret_cast<__nv_bfloat162*>(out.hi[g] + off) = h;
+      *reinterpret_cast<__nv_bfloat162*>(out.lo[g] + off) = l;
     }
   }
 }
