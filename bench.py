@@ -638,8 +638,7 @@ def run_ours(args, rank, world, dist):
         roofs.update({"contract": ("fp64", "TFLOP/s", "k_chi0_fp64"), "rho": ("fp64", "TFLOP/s", "k_rho_pairs"),
                       "wf_grid": ("fp64", "TFLOP/s", "k_wf_to_mixed")})
     bound, unit, kname = roofs[dom]
-    if dom == "contract" and args.real_axis:
-        kname = "k_herk_bf16x3"   # complex weights: every 128 x 128 tile
+    # (complex weights of real frequencies: the same kernel over every tile)
     extra = {}
     if unit == "GB/s":
         achieved = st_bytes[dom] / (per_step_ms[dom] * 1e-3) / 1e9

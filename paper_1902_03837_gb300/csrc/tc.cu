@@ -492,7 +492,7 @@ __global__ void __maxnreg__(144)
 k_herk_wide(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
             const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl, int total_kb,
             int kb_per_split, int mpad, double2* __restrict__ part, int ntiles, int nunits,
-            int* __restrict__ err, int nI, const int2* __restrict__ ranges) {
+            int* __restrict__ err, int nI, const int2* __restrict__ ranges, int full) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -555,7 +555,12 @@ k_herk_wide(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ C
       bool ok = true;
       for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         int I, J, kb0, nkb;
-        wide_decode(u % ntiles, nI, I, J);
+        if (full) {   // every tile: I fastest
+          I = (u % ntiles) % nI;
+          J = (u % ntiles) / nI;
+        } else {
+          wide_decode(u % ntiles, nI, I, J);
+        }
         unit_range(u, kb0, nkb);
         for (int k = 0; k < nkb; ++k, ++gk) {
           const int st = gk % kWStages;
@@ -850,17 +855,19 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nchunks, int n
 }
 
 // chi[i][j] = sum over chunks of the partials of the full tile grid (A rows i,
-// B rows j: tile (i / 64) + (j / 64) nT), every entry (no Hermitian symmetry).
+// B rows j: tile (i / 64) + (j / cols) nT with cols = 64 complex columns per
+// 128 x 128 tile or 128 per 128 x 256 tile), every entry (no Hermitian
+// symmetry).
 __global__ void k_tc_reduce_full(const double2* __restrict__ part, int nchunks, int ntiles, int nT, int ng,
-                                 double2* __restrict__ chi, int accumulate) {
+                                 double2* __restrict__ chi, int accumulate, int cols) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)ng * ng) return;
   const int i = (int)(e / ng), j = (int)(e % ng);
-  const int tile = i / (kBM / 2) + (j / (kBN / 2)) * nT;
-  const size_t off = (size_t)(i % (kBM / 2)) * (kBN / 2) + (j % (kBN / 2));
+  const int tile = i / (kBM / 2) + (j / cols) * nT;
+  const size_t off = (size_t)(i % (kBM / 2)) * cols + (j % cols);
   double sx = 0.0, sy = 0.0;
   for (int c = 0; c < nchunks; ++c) {
-    const double2 v = part[((size_t)c * ntiles + tile) * (kBM / 2) * (kBN / 2) + off];
+    const double2 v = part[((size_t)c * ntiles + tile) * (kBM / 2) * cols + off];
     sx += v.x;
     sy += v.y;
   }
@@ -909,7 +916,7 @@ cudaError_t launch_herm(chi0_ctx* c, TcState& t, int g, int kbpc, int nunits, co
   if (t.wide)
     k_herk_wide<<<grid, kWThreads, kWSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], mbh, mbl, t.total_kb, kbpc, t.mpad,
                                                           (double2*)t.part.p, t.ntiles, nunits, (int*)c->d_err.p,
-                                                          t.nI, ranges);
+                                                          t.nI, ranges, 0);
   else
     k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], mbh, mbl, t.total_kb, kbpc, t.mpad,
                                                           (double2*)t.part.p, t.ntiles, nunits, (int*)c->d_err.p, 0,
@@ -983,7 +990,8 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   };
   choose_split(t.ntiles, t.kbpc, t.nchunks);
   // the full tile grid of the complex contraction of a real-axis frequency
-  t.ntiles_f = nT * nT;
+  // (128 x 256 tiles with the wide kernel)
+  t.ntiles_f = t.wide ? nT * (t.mpad / kWN) : nT * nT;
   choose_split(t.ntiles_f, t.kbpc_f, t.nchunks_f);
   if (t.kpad / kPT > 0x7fffffff / t.mpad)
     return ctx_fail(c, CHI0_EUNSUPPORTED, "too many transitions for one contraction");
@@ -1000,7 +1008,8 @@ chi0_status tc_plan(chi0_ctx* c, int64_t nt, int ng, int nw) {
   // partials, for the split candidates of tc_tune_split
   const size_t room = c->group_cap > 0 ? 2 : 1;
   const size_t nbytes = std::max((size_t)t.nchunks * t.ntiles * room * t.tile_elems,
-                                  c->has_real ? (size_t)t.nchunks_f * t.ntiles_f * (kBM / 2) * (kBN / 2) : (size_t)0);
+                                  c->has_real ? (size_t)t.nchunks_f * t.ntiles_f * (kBM / 2) * (t.wide ? kWN : kBN) / 2
+                                              : (size_t)0);
   if ((s = ctx_ensure(c, t.part, nbytes * 16, "chunk partials")) != CHI0_OK)
     return s;
   // A buffers for up to kPrepGroup frequencies, as far as half of the free
@@ -1254,9 +1263,14 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       double2* out = chi + (size_t)jb.v * n2;
       stage_begin(c, CHI0_STAGE_CONTRACT);
       if (jb.cplx) {
-        k_herk_bf16x3<<<hgrid_f, kThreads, kSmemBytes, c->st>>>(
-            t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
-            nunits_f, (int*)c->d_err.p, nT, t.mpad, 0, nullptr);
+        if (t.wide)
+          k_herk_wide<<<hgrid_f, kWThreads, kWSmemBytes, c->st>>>(
+              t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
+              nunits_f, (int*)c->d_err.p, nT, nullptr, 1);
+        else
+          k_herk_bf16x3<<<hgrid_f, kThreads, kSmemBytes, c->st>>>(
+              t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
+              nunits_f, (int*)c->d_err.p, nT, t.mpad, 0, nullptr);
         ++nfull;
       } else {
         launch_herm(c, t, g, t.kbpc, nunits, nullptr, one_op);
@@ -1265,8 +1279,8 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       stage_end(c, CHI0_STAGE_CONTRACT, 1);
       stage_begin(c, CHI0_STAGE_REDUCE);
       if (jb.cplx)
-        k_tc_reduce_full<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks_f,
-                                                                           t.ntiles_f, nT, ng, out, accumulate);
+        k_tc_reduce_full<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>(
+            (const double2*)t.part.p, t.nchunks_f, t.ntiles_f, nT, ng, out, accumulate, (t.wide ? kWN : kBN) / 2);
       else
         k_tc_reduce<<<(unsigned)((n2 + 255) / 256), 256, 0, c->st>>>((const double2*)t.part.p, t.nchunks, t.ntiles,
                                                                       ng, out, accumulate, t.wide, t.nI,
@@ -1288,7 +1302,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
     }
   }
   const double tile_bytes = (double)t.tile_elems * 16;
-  const double tile_bytes_f = (double)(kBM / 2) * (kBN / 2) * 16;
+  const double tile_bytes_f = (double)(kBM / 2) * ((t.wide ? kWN : kBN) / 2) * 16;
   // operand split: R read once per pass, hi/lo written (B once if needed, A per job)
   c->stage[CHI0_STAGE_WEIGHTS].bytes += (double)(passes + (need_b ? 1 : 0)) * nt * ng * 8 +
                                         (double)(jobs.size() + (need_b ? 1 : 0)) * 4.0 * t.mpad * t.kpad;
@@ -1302,7 +1316,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
       (double)(nherm + nfull) * n2 * 16;
   // tensor-core work actually issued: 3 BF16 products over the tiles of each launch
   c->tc_issued_flops = 3.0 * 2.0 * kBM * (double)t.kpad *
-                      ((double)(t.wide ? kWN : kBN) * t.ntiles * nherm + (double)kBN * t.ntiles_f * nfull);
+                      ((double)(t.wide ? kWN : kBN) * (t.ntiles * nherm + t.ntiles_f * nfull));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
