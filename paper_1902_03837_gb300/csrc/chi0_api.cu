@@ -389,14 +389,90 @@ cudaError_t launch_wf_range(chi0_ctx* c, void* U, int k0, int nkr, int b0, int n
 // kernels of compute_rho (wavefunctions to the mixed grid; rho unless the
 // caller runs rho for many problems in one batched launch, or the
 // transitions are streamed in band blocks by build_chi0)
+// rho of the whole problem, pipelined with the coefficient upload: the k
+// points in kWfChunks chunks, each transformed once its copies have landed
+// (the event of its latest copy on the upload stream), and rho launched on a
+// chunk of k-pairs right after the transform that completes the grids of
+// its k and k - q points.  The blocks compute the same transitions as one
+// launch over all k-pairs, so the result is the same.
+constexpr int kWfChunks = 8;
+
+chi0_status launch_rho_pipelined(chi0_ctx* c) {
+  const int nk = c->nk, nch = std::min(kWfChunks, nk);
+  const int per = (nk + nch - 1) / nch;
+  auto chunk_of = [&](int k) { return k / per; };
+  // the transform chunk each rho chunk waits for
+  std::vector<int> need(nch, 0);
+  for (int k = 0; k < nk; ++k) {
+    const int ch = chunk_of(k);
+    need[ch] = std::max(need[ch], std::max(ch, chunk_of(c->h_kq[k])));
+  }
+  const RhoGeom& g0 = c->geom;
+  const size_t band = (size_t)g0.N1 * g0.NZ * g0.N2;   // complex entries of one band's mixed grid
+  const size_t cbytes = cplx_bytes(c);
+  for (int w = 0; w * per < nk; ++w) {
+    const int k0 = w * per, k1 = std::min(nk, k0 + per);
+    if (!c->ev_up.empty()) {   // the chunk's latest copy
+      int last = -1;
+      for (int k = k0; k < k1; ++k)
+        if (c->up_seq[k] >= 0 && (last < 0 || c->up_seq[k] > c->up_seq[last])) last = k;
+      if (last >= 0) CK(cudaStreamWaitEvent(c->st, c->ev_up[last], 0), "upload wait");
+    }
+    // the transform of k0 .. k1 - 1, written at its global place in U
+    cudaError_t e = launch_wf_range(c, (char*)c->d_U.p + (size_t)k0 * c->nb * band * cbytes, k0, k1 - k0, 0, c->nb);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    if (k1 == nk && c->ev_wf_done) CK(cudaEventRecord(c->ev_wf_done, c->st), "upload event");
+    for (int r = 0; r < nch; ++r) {
+      if (need[r] != w) continue;
+      const int r0 = r * per, r1 = std::min(nk, r0 + per);
+      RhoGeom g = g0;
+      g.k0 = r0;
+      g.nk = r1 - r0;
+      g.nbu = c->nb;
+      g.bu0 = 0;
+      g.nbm = c->nb;
+      const size_t roff = (size_t)r0 * c->Nn * c->Nm * g0.ng;
+      const size_t uoff = (size_t)r0 * c->nb * band;
+      chi0::stage_begin(c, CHI0_STAGE_RHO);
+      if (c->fp64)
+        e = chi0::launch_rho_pairs<double, double2>(
+            g, (const double2*)c->d_U.p + uoff, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+            (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const double2*)c->d_tw1.p,
+            (const double2*)c->d_tw2.p, (double2*)c->d_R.p + roff, c->st, (const double2*)c->d_U.p);
+      else
+        e = chi0::launch_rho_pairs<float, float2>(
+            g, (const float2*)c->d_U.p + uoff, (const int32_t*)c->d_kq.p, (const int32_t*)c->d_g0.p,
+            (const int32_t*)c->d_gresp.p, (const int32_t*)c->d_gperm.p, (const float2*)c->d_tw1.p,
+            (const float2*)c->d_tw2.p, (float2*)c->d_R.p + roff, c->st, (const float2*)c->d_U.p);
+      if (e != cudaSuccess) return cuda_fail(c, e, "rho_pairs launch");
+      chi0::stage_end(c, CHI0_STAGE_RHO, 1);
+    }
+  }
+  return CHI0_OK;
+}
+
 chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
   const int iq = c->plan_rho_iq;
   if (iq < 0) return fail(c, CHI0_ESTATE, "rho not planned");
+  if (with_pairs && c->nt > 0 && !c->grid_shared && c->stream_nb == 0 && c->nk >= 2 * kWfChunks) {
+    chi0_status s = launch_rho_pipelined(c);
+    if (s != CHI0_OK) return s;
+    c->rho_iq = iq;
+    c->chi_iq = c->eps_iq = -1;
+    return CHI0_OK;
+  }
   if (c->nt > 0 && !c->grid_shared) {
     // streamed: the grids of the m bands 0 .. Nm - 1 at every k only
     const int nkr = c->stream_nb > 0 ? c->nk : 0, nbo = c->stream_nb > 0 ? c->Nm : 0;
+    if (!c->ev_up.empty()) {   // every copy on the upload stream first
+      int last = -1;
+      for (int k = 0; k < c->nk; ++k)
+        if (c->up_seq[k] >= 0 && (last < 0 || c->up_seq[k] > c->up_seq[last])) last = k;
+      if (last >= 0) CK(cudaStreamWaitEvent(c->st, c->ev_up[last], 0), "upload wait");
+    }
     cudaError_t e = launch_wf_range(c, c->d_U.p, 0, nkr, 0, nbo);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
+    if (c->ev_wf_done) CK(cudaEventRecord(c->ev_wf_done, c->st), "upload event");
   }
   if (c->nt > 0 && c->stream_nb == 0) {
     const RhoGeom& g = c->geom;
@@ -1288,6 +1364,9 @@ chi0_status chi0_set_wavefunctions(chi0_ctx* c, int ik, int npw, const int32_t* 
       !c->wf_set[ik] || c->h_npw[ik] != npw || std::memcmp(hg, incoming.data(), (size_t)npw * 12) != 0;
   const bool same = (coef_is_c64 != 0) == !c->fp64;
   char* dst = (char*)c->d_coef.p + (size_t)ik * c->nb * c->npw_max * cb;
+  // a copy of this k point still queued on the upload stream comes first
+  if (!c->ev_up.empty() && !(same && !on_device && !new_sphere))
+    CK(cudaStreamWaitEvent(c->st, c->ev_up[ik], 0), "upload wait");
   if (new_sphere) {
     ++c->plan_epoch;
     std::memcpy(hg, incoming.data(), (size_t)npw * 12);
@@ -1302,7 +1381,25 @@ chi0_status chi0_set_wavefunctions(chi0_ctx* c, int ik, int npw, const int32_t* 
     // coefficients: rows of npw, padded to npw_max
     CK(cudaMemsetAsync(dst, 0, (size_t)c->nb * c->npw_max * cb, c->st), "zero coefficients");
   }
-  if (same) {
+  if (same && !on_device && !new_sphere) {
+    // new values on the same sphere: copy on the upload stream (see s_up)
+    if (!c->s_up) {
+      CK(cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking), "upload stream");
+      CK(cudaEventCreateWithFlags(&c->ev_wf_done, cudaEventDisableTiming), "upload event");
+    }
+    if (c->ev_up.empty()) {
+      c->ev_up.assign(c->nk, nullptr);
+      c->up_seq.assign(c->nk, -1);
+      for (int k = 0; k < c->nk; ++k)
+        CK(cudaEventCreateWithFlags(&c->ev_up[k], cudaEventDisableTiming), "upload event");
+    }
+    CK(cudaStreamWaitEvent(c->s_up, c->ev_wf_done, 0), "upload wait");
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->npw_max * cb, coef, (size_t)npw * cb, (size_t)npw * cb, c->nb,
+                         cudaMemcpyHostToDevice, c->s_up),
+       "coefficients copy");
+    CK(cudaEventRecord(c->ev_up[ik], c->s_up), "upload event");
+    c->up_seq[ik] = c->up_count++;
+  } else if (same) {
     CK(cudaMemcpy2DAsync(dst, (size_t)c->npw_max * cb, coef, (size_t)npw * cb, (size_t)npw * cb,
                          c->nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          c->st),
@@ -1772,7 +1869,7 @@ void chi0_destroy(chi0_ctx* c) {
       if (e) cudaEventDestroy(e);
   chi0::tc_release(c);
   chi0::sig_tc_release(c);
-  cudaStream_t pst[] = {c->s_ct, c->s_dy, c->s_dy2};
+  cudaStream_t pst[] = {c->s_ct, c->s_dy, c->s_dy2, c->s_up};
   for (cudaStream_t t : pst)
     if (t) {
       cudaStreamSynchronize(t);
@@ -1785,6 +1882,9 @@ void chi0_destroy(chi0_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_prep)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_up)
+    if (e) cudaEventDestroy(e);
+  if (c->ev_wf_done) cudaEventDestroy(c->ev_wf_done);
   delete c;
 }
 

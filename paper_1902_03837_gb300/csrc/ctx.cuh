@@ -141,6 +141,17 @@ struct chi0_ctx {
   // (highest priority), both forked from and joined back into st
   cudaStream_t s_ct = nullptr, s_dy = nullptr;
   cudaStream_t s_dy2 = nullptr;      // second Dyson stream: consecutive groups alternate
+  // Coefficients set from host memory on an unchanged sphere are copied on
+  // s_up, one event per k point (ev_up[k], with the copy's sequence number
+  // up_seq[k]), after the last wavefunction transform that read the previous
+  // ones (ev_wf_done).  compute_rho then transforms the k points in chunks as
+  // their copies land and starts rho on a chunk of k-pairs as soon as the
+  // grids of its k and k - q points are there, so the upload overlaps rho.
+  cudaStream_t s_up = nullptr;
+  std::vector<cudaEvent_t> ev_up;
+  std::vector<int64_t> up_seq;
+  int64_t up_count = 0;
+  cudaEvent_t ev_wf_done = nullptr;
   cudaEvent_t ev_join_dy2 = nullptr;
   std::vector<cudaEvent_t> ev_freq;  // [nw] contraction (and reduction) of frequency w done
   std::vector<cudaEvent_t> ev_prep;  // [nw] operand split of frequency w done
