@@ -492,7 +492,8 @@ __global__ void __maxnreg__(144)
 k_herk_wide(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
             const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl, int total_kb,
             int kb_per_split, int mpad, double2* __restrict__ part, int ntiles, int nunits,
-            int* __restrict__ err, int nI, const int2* __restrict__ ranges, int full) {
+            int* __restrict__ err, int nI, const int2* __restrict__ ranges, int full, int mpad_b,
+            int f32out) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -571,13 +572,13 @@ k_herk_wide(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ C
           }
           const uint32_t sb = base + st * kWStageBytes;
           mbar_expect_tx(bar_full + 8 * st, kWStageBytes);
-          const int row = (kb0 + k) * mpad;
+          const int row = (kb0 + k) * mpad, rowb = (kb0 + k) * mpad_b;
           tma_load_2d(sb, &tm_ah, 0, row + I * kBM, bar_full + 8 * st);
           tma_load_2d(sb + kWTileA, &tm_al, 0, row + I * kBM, bar_full + 8 * st);
-          tma_load_2d(sb + 2 * kWTileA, &tm_bh, 0, row + J * kWN, bar_full + 8 * st);
-          tma_load_2d(sb + 2 * kWTileA + kWTileA, &tm_bh, 0, row + J * kWN + kBM, bar_full + 8 * st);
-          tma_load_2d(sb + 2 * kWTileA + kWTileB, &tm_bl, 0, row + J * kWN, bar_full + 8 * st);
-          tma_load_2d(sb + 2 * kWTileA + kWTileB + kWTileA, &tm_bl, 0, row + J * kWN + kBM, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA, &tm_bh, 0, rowb + J * kWN, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA + kWTileA, &tm_bh, 0, rowb + J * kWN + kBM, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA + kWTileB, &tm_bl, 0, rowb + J * kWN, bar_full + 8 * st);
+          tma_load_2d(sb + 2 * kWTileA + kWTileB + kWTileA, &tm_bl, 0, rowb + J * kWN + kBM, bar_full + 8 * st);
         }
       }
     } else if (warp == 1 && lane == 0) {
@@ -676,15 +677,34 @@ k_herk_wide(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ C
       }
       if (!ok) break;
       const int il = (q * 32 + lane) >> 1;  // complex row of the tile
-      double2* out = part + (size_t)u * kWPart + (size_t)il * (kWN / 2) + hcol * (kBN / 2) + (odd ? 4 : 0);
+      if (f32out) {
+        // the compensated sums rounded to FP32, written as the 64 x 64
+        // complex tiles of the full grid of 128-row B tiles: this warp's 64
+        // columns are tile I + (2 J + hcol) nI (one k range per tile), which
+        // exists while its B rows lie within mpad_b
+        const int tile = u % ntiles, I = tile % nI, Jn = 2 * (tile / nI) + hcol;
+        if (Jn * kBN < mpad_b) {
+          float2* out = reinterpret_cast<float2*>(part) + ((size_t)Jn * nI + I) * (size_t)(kBM / 2) * (kBN / 2) +
+                        (size_t)il * (kBN / 2) + (odd ? 4 : 0);
 #pragma unroll
-      for (int cb = 0; cb < kBN / 16; ++cb)
+          for (int cb = 0; cb < kBN / 16; ++cb)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int e = cb * 4 + jj;
-          out[cb * 8 + jj] = make_double2((double)accs[e][0] + (double)accc[e][0],
-                                          (double)accs[e][1] + (double)accc[e][1]);
+            for (int jj = 0; jj < 4; ++jj) {
+              const int e = cb * 4 + jj;
+              out[cb * 8 + jj] = make_float2(accs[e][0] + accc[e][0], accs[e][1] + accc[e][1]);
+            }
         }
+      } else {
+        double2* out = part + (size_t)u * kWPart + (size_t)il * (kWN / 2) + hcol * (kBN / 2) + (odd ? 4 : 0);
+#pragma unroll
+        for (int cb = 0; cb < kBN / 16; ++cb)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int e = cb * 4 + jj;
+            out[cb * 8 + jj] = make_double2((double)accs[e][0] + (double)accc[e][0],
+                                            (double)accs[e][1] + (double)accc[e][1]);
+          }
+      }
     }
   }
   tc_fence_before();
@@ -916,7 +936,7 @@ cudaError_t launch_herm(chi0_ctx* c, TcState& t, int g, int kbpc, int nunits, co
   if (t.wide)
     k_herk_wide<<<grid, kWThreads, kWSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], mbh, mbl, t.total_kb, kbpc, t.mpad,
                                                           (double2*)t.part.p, t.ntiles, nunits, (int*)c->d_err.p,
-                                                          t.nI, ranges, 0);
+                                                          t.nI, ranges, 0, t.mpad, 0);
   else
     k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah[g], t.m_al[g], mbh, mbl, t.total_kb, kbpc, t.mpad,
                                                           (double2*)t.part.p, t.ntiles, nunits, (int*)c->d_err.p, 0,
@@ -1266,7 +1286,7 @@ chi0_status tc_launch(chi0_ctx* c, const void* R, const double* w, int64_t nt, i
         if (t.wide)
           k_herk_wide<<<hgrid_f, kWThreads, kWSmemBytes, c->st>>>(
               t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
-              nunits_f, (int*)c->d_err.p, nT, nullptr, 1);
+              nunits_f, (int*)c->d_err.p, nT, nullptr, 1, t.mpad, 0);
         else
           k_herk_bf16x3<<<hgrid_f, kThreads, kSmemBytes, c->st>>>(
               t.m_ah[g], t.m_al[g], t.m_bh, t.m_bl, t.total_kb, t.kbpc_f, t.mpad, (double2*)t.part.p, t.ntiles_f,
@@ -1539,9 +1559,9 @@ chi0_status sig_tc_plan(chi0_ctx* c, int64_t T, int ng) {
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   t.nsm = std::max(1, nsm);
-  cudaError_t e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_herk_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_herk_bf16x3, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_herk_wide, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return ctx_fail(c, CHI0_ECUDA, cudaGetErrorString(e));
   return CHI0_OK;
@@ -1561,14 +1581,18 @@ cudaError_t sig_tc_split_a(chi0_ctx* c, const double2* E, const double* vsqrt) {
   return cudaGetLastError();
 }
 
+// Y on the wide kernel: 128 x 256 tiles over the full grid (nJ / 2 wide
+// column tiles, rounded up), one k range per tile, written as Y's 64 x 64
+// complex FP32 tiles; the half of a last wide tile beyond the B rows is not
+// written.
 cudaError_t sig_tc_contract(chi0_ctx* c, float2* Y) {
   SigTc& t = *static_cast<SigTc*>(c->sig_tc);
-  const int ntiles = t.nI * t.nJ;
+  const int ntiles = t.nI * ((t.nJ + 1) / 2);
   const int total_kb = (int)(t.kpad / kBK);
   const unsigned grid = (unsigned)std::min(ntiles, t.nsm);
-  k_herk_bf16x3<<<grid, kThreads, kSmemBytes, c->st>>>(t.m_ah, t.m_al, t.m_bh, t.m_bl, total_kb, total_kb,
-                                                        t.mpad_a, reinterpret_cast<double2*>(Y), ntiles, ntiles,
-                                                        (int*)c->d_err.p, t.nI, (int)t.mpad_b, 1, nullptr);
+  k_herk_wide<<<grid, kWThreads, kWSmemBytes, c->st>>>(t.m_ah, t.m_al, t.m_bh, t.m_bl, total_kb, total_kb, t.mpad_a,
+                                                        reinterpret_cast<double2*>(Y), ntiles, ntiles,
+                                                        (int*)c->d_err.p, t.nI, nullptr, 1, (int)t.mpad_b, 1);
   return cudaGetLastError();
 }
 
