@@ -39,10 +39,13 @@
 // Every mbarrier wait is bounded: on timeout the kernel raises the device
 // error flag (reported as CHI0_ETIMEOUT), skips the remaining work, frees its
 // TMEM and returns.
-// The Hermitian contraction (real weights) runs the wide variant of this
-// kernel, k_herk_wide: 128 x 256 tiles, N = 256 products, twelve warps (see
-// its comment); the full tile grid (complex weights of a real frequency, the
-// self-energy product) keeps the 128 x 128 kernel.
+// Every contraction now runs the wide variant of this kernel, k_herk_wide:
+// 128 x 256 tiles, N = 256 products, twelve warps (see its comment), over the
+// lower-triangle tiles (real weights), over every tile (the complex weights
+// of a real frequency), or over every tile with FP32 tiles out (the
+// self-energy product).  k_herk_bf16x3 below, the 128 x 128 form, is no longer
+// launched; its comment describes the work units and the pipeline that
+// k_herk_wide widens.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
