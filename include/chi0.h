@@ -116,10 +116,14 @@ chi0_status chi0_create(const chi0_config* cfg, chi0_ctx** out);
  *   on_device: 1 if gvec and coef are device pointers (copied device to device),
  *              0 if host pointers (copied; pinned host memory makes the copy async).
  * The data are copied (converted to the working precision when needed); the
- * caller keeps ownership of its buffers, which may be reused once the call has
- * returned for host pointers, or once the stream has passed this point for
- * device pointers.  Errors: CHI0_EINVAL (ik or npw out of range, NULL),
- * CHI0_ENOMEM, CHI0_ECUDA. */
+ * caller keeps ownership of its buffers.  Pageable host buffers may be reused
+ * once the call has returned.  Pinned host coefficients are copied
+ * asynchronously: on an unchanged sphere the copy runs on an internal upload
+ * stream that chi0_compute_rho overlaps with its transforms and rho; the
+ * buffer may be reused after chi0_synchronize, or after any call that
+ * returns results to the host and follows the next chi0_compute_rho.  Device
+ * buffers may be reused once the context's stream has passed this point.
+ * Errors: CHI0_EINVAL (ik or npw out of range, NULL), CHI0_ENOMEM, CHI0_ECUDA. */
 chi0_status chi0_set_wavefunctions(chi0_ctx* ctx, int ik, int npw, const int32_t* gvec,
                                    const void* coef, int coef_is_c64, int on_device);
 

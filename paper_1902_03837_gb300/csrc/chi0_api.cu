@@ -1816,6 +1816,7 @@ chi0_status chi0_check_bounded_wait(chi0_ctx* c) {
 
 chi0_status chi0_synchronize(chi0_ctx* c) {
   if (!c) return CHI0_EINVAL;
+  if (c->s_up) CK(cudaStreamSynchronize(c->s_up), "synchronize");   // coefficient copies in flight
   CK(cudaStreamSynchronize(c->st), "synchronize");
   CK(cudaGetLastError(), "pending error");
   return check_device_error(c);
