@@ -40,6 +40,8 @@
 
 struct chi0_batch {
   std::vector<chi0_ctx*> items;  // one problem context per (context, q index) pair
+  std::vector<chi0_ctx*> bases;  // the distinct caller contexts whose coefficients the problems read
+  cudaEvent_t ev_up = nullptr;   // their pending coefficient copies, ahead of a replay
   std::vector<int> iqs;
   std::vector<void*> outs;       // eps~^-1 per problem (NULL: no Dyson step)
   std::vector<void*> chi_outs;   // chi0 per problem (NULL: not copied out)
@@ -197,6 +199,7 @@ void destroy_batch(chi0_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaEvent_t e : b->evs) cudaEventDestroy(e);
+  if (b->ev_up) cudaEventDestroy(b->ev_up);
   if (b->tasks.p) cudaFree(b->tasks.p);
   if (b->counter.p) cudaFree(b->counter.p);
   b->tasks = b->counter = DevBuf{};
@@ -260,6 +263,12 @@ chi0_status chi0_batch_create(chi0_ctx* const* ctxs, const int* iqs, void* const
       if (!ctxs[i]->wf_set[k] || !ctxs[i]->energies_set) s = CHI0_ESTATE;
     chi0_ctx* c = s == CHI0_OK ? chi0::make_problem_ctx(ctxs[i]) : nullptr;
     if (s == CHI0_OK && !c) s = CHI0_ENOMEM;
+    if (s == CHI0_OK && std::find(b->bases.begin(), b->bases.end(), ctxs[i]) == b->bases.end()) {
+      b->bases.push_back(ctxs[i]);
+      // coefficient copies still on the caller context's upload stream land
+      // before the planning and tuning below read the coefficients
+      if (ctxs[i]->s_up && cudaStreamSynchronize(ctxs[i]->s_up) != cudaSuccess) s = CHI0_ECUDA;
+    }
     if (c) {
       c->group_cap = 4;
       b->items.push_back(c);
@@ -459,10 +468,27 @@ chi0_status chi0_batch_run(chi0_batch* b, void* stream) {
       return CHI0_ECUDA;
     }
   }
+  // the replay reads the callers' coefficients: it follows their copies on
+  // the upload streams, and their next copies wait for it (ev_wf_done)
+  for (chi0_ctx* base : b->bases) {
+    if (!base->s_up) continue;
+    if ((!b->ev_up && cudaEventCreateWithFlags(&b->ev_up, cudaEventDisableTiming) != cudaSuccess) ||
+        cudaEventRecord(b->ev_up, base->s_up) != cudaSuccess ||
+        cudaStreamWaitEvent((cudaStream_t)stream, b->ev_up, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return CHI0_ECUDA;
+    }
+  }
   if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();
     return CHI0_ECUDA;
   }
+  for (chi0_ctx* base : b->bases)
+    if ((!base->ev_wf_done && cudaEventCreateWithFlags(&base->ev_wf_done, cudaEventDisableTiming) != cudaSuccess) ||
+        cudaEventRecord(base->ev_wf_done, (cudaStream_t)stream) != cudaSuccess) {
+      cudaGetLastError();
+      return CHI0_ECUDA;
+    }
   b->last_stream = (cudaStream_t)stream;
   b->replayed = true;
   return CHI0_OK;

@@ -1383,10 +1383,8 @@ chi0_status chi0_set_wavefunctions(chi0_ctx* c, int ik, int npw, const int32_t* 
   }
   if (same && !on_device && !new_sphere) {
     // new values on the same sphere: copy on the upload stream (see s_up)
-    if (!c->s_up) {
-      CK(cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking), "upload stream");
-      CK(cudaEventCreateWithFlags(&c->ev_wf_done, cudaEventDisableTiming), "upload event");
-    }
+    if (!c->s_up) CK(cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking), "upload stream");
+    if (!c->ev_wf_done) CK(cudaEventCreateWithFlags(&c->ev_wf_done, cudaEventDisableTiming), "upload event");
     if (c->ev_up.empty()) {
       c->ev_up.assign(c->nk, nullptr);
       c->up_seq.assign(c->nk, -1);
