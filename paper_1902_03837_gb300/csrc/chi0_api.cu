@@ -383,6 +383,9 @@ cudaError_t launch_wf_range(chi0_ctx* c, void* U, int k0, int nkr, int b0, int n
                                         (const float2*)c->d_coef.p, (const float2*)c->d_tw1.p,
                                         (const float2*)c->d_tw2.p, (float2*)U, c->st, k0, nkr, b0, nbo);
   if (e == cudaSuccess) chi0::stage_end(c, CHI0_STAGE_WF_GRID, 1);
+  // the coefficients have been read up to here: the next copy on the upload
+  // stream waits for this point
+  if (e == cudaSuccess && c->ev_wf_done && !c->capturing) e = cudaEventRecord(c->ev_wf_done, c->st);
   return e;
 }
 
@@ -421,7 +424,6 @@ chi0_status launch_rho_pipelined(chi0_ctx* c) {
     // the transform of k0 .. k1 - 1, written at its global place in U
     cudaError_t e = launch_wf_range(c, (char*)c->d_U.p + (size_t)k0 * c->nb * band * cbytes, k0, k1 - k0, 0, c->nb);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
-    if (k1 == nk && c->ev_wf_done) CK(cudaEventRecord(c->ev_wf_done, c->st), "upload event");
     for (int r = 0; r < nch; ++r) {
       if (need[r] != w) continue;
       const int r0 = r * per, r1 = std::min(nk, r0 + per);
@@ -472,7 +474,6 @@ chi0_status launch_rho(chi0_ctx* c, bool with_pairs) {
     }
     cudaError_t e = launch_wf_range(c, c->d_U.p, 0, nkr, 0, nbo);
     if (e != cudaSuccess) return cuda_fail(c, e, "wf_to_mixed launch");
-    if (c->ev_wf_done) CK(cudaEventRecord(c->ev_wf_done, c->st), "upload event");
   }
   if (c->nt > 0 && c->stream_nb == 0) {
     const RhoGeom& g = c->geom;
@@ -1384,7 +1385,10 @@ chi0_status chi0_set_wavefunctions(chi0_ctx* c, int ik, int npw, const int32_t* 
   if (same && !on_device && !new_sphere) {
     // new values on the same sphere: copy on the upload stream (see s_up)
     if (!c->s_up) CK(cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking), "upload stream");
-    if (!c->ev_wf_done) CK(cudaEventCreateWithFlags(&c->ev_wf_done, cudaEventDisableTiming), "upload event");
+    if (!c->ev_wf_done) {   // the first copy waits for everything queued on the context's stream
+      CK(cudaEventCreateWithFlags(&c->ev_wf_done, cudaEventDisableTiming), "upload event");
+      CK(cudaEventRecord(c->ev_wf_done, c->st), "upload event");
+    }
     if (c->ev_up.empty()) {
       c->ev_up.assign(c->nk, nullptr);
       c->up_seq.assign(c->nk, -1);
