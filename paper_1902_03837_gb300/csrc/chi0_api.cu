@@ -401,8 +401,9 @@ cudaError_t launch_wf_range(chi0_ctx* c, void* U, int k0, int nkr, int b0, int n
 constexpr int kWfChunks = 8;
 
 chi0_status launch_rho_pipelined(chi0_ctx* c) {
-  const int nk = c->nk, nch = std::min(kWfChunks, nk);
-  const int per = (nk + nch - 1) / nch;
+  const int nk = c->nk;
+  const int per = (nk + kWfChunks - 1) / kWfChunks;   // k points per chunk
+  const int nch = (nk + per - 1) / per;                // chunks (the last may be short)
   auto chunk_of = [&](int k) { return k / per; };
   // the transform chunk each rho chunk waits for
   std::vector<int> need(nch, 0);
@@ -413,7 +414,7 @@ chi0_status launch_rho_pipelined(chi0_ctx* c) {
   const RhoGeom& g0 = c->geom;
   const size_t band = (size_t)g0.N1 * g0.NZ * g0.N2;   // complex entries of one band's mixed grid
   const size_t cbytes = cplx_bytes(c);
-  for (int w = 0; w * per < nk; ++w) {
+  for (int w = 0; w < nch; ++w) {
     const int k0 = w * per, k1 = std::min(nk, k0 + per);
     if (!c->ev_up.empty()) {   // the chunk's latest copy
       int last = -1;
